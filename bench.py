@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the fused moment-represented LB step on GB300 (MLUPS and HBM roofline).
+
+Headline workload: D3Q19, FP32 storage and arithmetic, 256^3 channel with bounce-back walls on
+y = 0 and y = 255, periodic in x and z, uniform body force 1e-6 along x, tau = 0.9, p* = rho - 1
+uniform in [-1e-3, 1e-3] (seeded). One step = one launch of the fused stream-collide kernel with
+the FP64 conservation sums fused in. The two moment buffers (2 x 671 MB) exceed the 129 MB L2, so
+no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on a bounded sample
+of the same workload on the host cores. Under torchrun every rank runs its own replica on its own
+GPU (the path is not sharded); the time is the max over ranks and the value the sum of all
+replicas' lattice updates per second.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & HBM GB/s (D3Q19/27, FP32 vs FP16-stored); adjoint/forward time ratio"
+WORKLOAD = ("D3Q19 regularized, moment-represented, FP32, 256^3 channel: bounce-back walls y=0,255, periodic x/z, "
+            "body force 1e-6 along x, tau=0.9, p* = rho-1 ~ U[-1e-3,1e-3] seed 1")
+SHAPE = (256, 256, 256)
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
+
+def algorithmic_bytes(storage, mask=False, field=False):
+    """Per lattice update: each of the 10 stored fields read once and written once, plus the
+    mask byte and a per-site FP32 force field when present."""
+    b = 20 * STORAGE_BYTES[storage]
+    if mask:
+        b += 1
+    if field:
+        b += 3 * (8 if storage == "f64" else 4)
+    return b
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha1()
+    for name in ("lattice.cuh", "stream_collide.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_09160_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(workload_key):
+    """dram bytes per launch recorded from an ncu capture of the current kernel source, else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = kernel_source_sha()
+    for line in open(path):
+        parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if parts.get("workload") == workload_key and parts.get("kernel_sha") == sha:
+            return float(parts["bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 100 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu_id)], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return None
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def gpu_identifier(torch, dev):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return str(dev)
+
+
+def channel_solver(torch, device, storage="f32", lattice=19, shape=SHAPE):
+    import synth
+    from paper_2609_09160_gb300 import Solver
+
+    M0, solid = synth.channel(shape, 1e-3, seed=1, dtype=torch.float32)
+    s = Solver(shape, lattice=lattice, tau=0.9, storage=storage, force=(1e-6, 0.0, 0.0), mask=solid, device=device)
+    return s, M0, solid
+
+
+def time_steps(torch, s, steps, warmup, barrier=None):
+    """Device time of `steps` fused steps (one kernel each) on the solver's stream."""
+    for _ in range(warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    if barrier is not None:
+        barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(s.stream)
+    for _ in range(steps):
+        s.step(1)
+    end.record(s.stream)
+    torch.cuda.synchronize()
+    if barrier is not None:
+        barrier()
+    return start.elapsed_time(end) / 1e3
+
+
+def e2e_measure(torch, device, steps):
+    """Same metric through the public API with host buffers: upload the public state from pinned
+    host memory, run the steps reading the FP64 conservation sums back to the host after every step
+    (one 48-byte read each), download the final state to pinned host memory."""
+    s, M0, _ = channel_solver(torch, device)
+    host_in = M0.pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    s.set_moments(host_in)
+    s.step(3)
+    s.reduce()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_moments(host_in)
+    for _ in range(steps):
+        s.step(1)
+        s.reduce()
+    s.moments(out=host_out)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    n = M0[0].numel()
+    nbytes = host_in.numel() * host_in.element_size()
+    return {"value": n * steps / t / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nbytes / steps,
+            "d2h_bytes_per_step": 48 + nbytes / steps}
+
+
+def cpu_baseline_oracle(target_seconds=12.0, shape=(4, 256, 256), max_steps=50):
+    """The FP64 oracle as it stands on the host cores, on a z-slab of the channel workload."""
+    import torch
+
+    import oracle
+    import synth
+
+    M0, solid = synth.channel(shape, 1e-3, seed=1)
+    t0 = time.perf_counter()
+    steps = 0
+    lat = oracle.D3Q19
+    F = oracle.lbm.as_field((1e-6, 0.0, 0.0), shape)
+    rho = oracle.lbm.as_scalar_field(1.0, shape)
+    om = oracle.lbm.as_scalar_field(oracle.lbm.omega_from_tau(0.9), shape)
+    f = oracle.lbm.populations_from_moments(lat, M0, F, rho)
+    while steps < max_steps and (steps < 2 or time.perf_counter() - t0 < target_seconds):
+        f = oracle.lbm.step(lat, f, F, rho, om, solid)
+        steps += 1
+    t = time.perf_counter() - t0
+    n = shape[0] * shape[1] * shape[2]
+    return {"value": n * steps / t / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{steps} population-form FP64 steps on a {shape[2]}x{shape[1]}x{shape[0]} (x,y,z) slab of the "
+                      "channel (walls y=0,255, periodic z)"}
+
+
+def extras(torch, device, quick):
+    """Secondary rows: D3Q27 512^3 storage dtypes, D3Q19 512^3, two-component, FP64, adjoint ratio."""
+    import synth
+    from paper_2609_09160_gb300 import Solver, rollout
+
+    out = {}
+    peak, _ = measured_peaks()
+
+    def rate(s, steps, warmup, bytes_per_lup):
+        t = time_steps(torch, s, steps, warmup)
+        n = s.N
+        mlups = n * steps / t / 1e6
+        return {"MLUPS": round(mlups, 1), "algorithmic_GBps": round(bytes_per_lup * mlups / 1e3, 1),
+                "hbm_frac_of_measured": round(bytes_per_lup * mlups / 1e3 / peak, 3), "steps": steps}
+
+    n = 512
+    M0 = synth.taylor_green_perturbed(n, 0.04, 0.55, 0.01, seed=3, dtype=torch.float32, device=device)
+    for lattice in (27, 19):
+        for storage in ("f32", "f16", "bf16"):
+            s = Solver((n, n, n), lattice=lattice, tau=0.55, storage=storage, device=device)
+            s.set_moments(M0)
+            out[f"tg512_d3q{lattice}_{storage}"] = rate(s, 30 if quick else 100, 5, algorithmic_bytes(storage))
+            del s
+            torch.cuda.empty_cache()
+    del M0
+    torch.cuda.empty_cache()
+
+    # two-component droplet, 128^3, R = 20, equal densities, tau = 1 (config of the Laplace test)
+    shape = (128, 128, 128)
+    phi0 = synth.droplet(shape, 20.0, 4.0, dtype=torch.float32, device=device)
+    s = Solver(shape, lattice=19, storage="f32", device=device,
+               two_component=dict(rho_l=1.0, rho_h=1.0, tau_l=1.0, tau_h=1.0, sigma=0.03, width=4.0, diffusivity=0.1))
+    s.set_moments(torch.zeros((10,) + shape, dtype=torch.float32, device=device), phi0)
+    r = rate(s, 50 if quick else 200, 5, algorithmic_bytes("f32") + 4 * (1 + 1 + 3 + 3) + 4 * 3 * 2)
+    r["note"] = "3 kernels per step (phase field advance, forces, fused LB)"
+    out["droplet128_d3q19_f32"] = r
+    del s
+
+    # FP64 parity mode: 32^3 Taylor-Green (launch-latency bound at this size)
+    s = Solver((32, 32, 32), lattice=19, tau=0.8, storage="f64", device=device)
+    s.set_moments(synth.taylor_green(32, 0.02, 0.8, device=device))
+    out["tg32_d3q19_f64"] = rate(s, 100, 5, algorithmic_bytes("f64"))
+    del s
+
+    # adjoint / forward time ratio: 128x64x64 channel, per-site force, 500 steps, checkpoints every 50
+    shape = (64, 64, 128)
+    mask = synth.channel_walls(shape)
+    F = synth.random_field(shape, 1e-6, seed=70, mask=mask).to(device=device, dtype=torch.float32)
+    F.requires_grad_(True)
+    u_tgt = synth.random_field(shape, 1e-4, seed=71).to(device=device, dtype=torch.float32)
+    fluid = (~mask).to(device=device, dtype=torch.float32)
+    s = Solver(shape, lattice=19, tau=0.9, storage="f32", force_field=F.detach(), mask=mask, device=device)
+    M0 = torch.zeros((10,) + shape, dtype=torch.float32, device=device)
+    T = 100 if quick else 500
+    for rep in range(2):  # first repetition warms up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        MT = rollout(F, M0, s, T, 50)
+        d = (MT[1:4] - u_tgt) * fluid
+        L = (d * d).sum() / fluid.sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        L.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        F.grad = None
+    out["adjoint_128x64x64_d3q19_f32"] = {"forward_s": round(t1 - t0, 4), "backward_s": round(t2 - t1, 4),
+                                          "ratio": round((t2 - t1) / (t1 - t0), 3), "steps": T, "checkpoint_every": 50}
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2609_09160_gb300 import build as _build
+
+    _build.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    barrier = None
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        barrier = dist.barrier
+    s, M0, solid = channel_solver(torch, device)
+    s.set_moments(M0.to(device))
+    with ClockSampler(gpu_identifier(torch, device)) as clk:
+        t = time_steps(torch, s, args.steps, args.warmup, barrier)
+    clocks = clk.summary()
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = tt.item()
+    n = s.N
+    value = world * n * args.steps / t / 1e6
+    sums = s.reduce()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peaks()
+    bpl = algorithmic_bytes("f32", mask=True)
+    t_launch = t / args.steps
+    achieved = bpl * n / t_launch / 1e9
+    traffic = ncu_traffic("channel256_d3q19_f32")
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "D3Q19", "shape_xyz": [256, 256, 256], "storage": "f32",
+                   "l2": "inputs larger than L2 (2 x 671 MB moment buffers), no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "k_stream_collide<D3Q19,float,8,mask>", "bytes_per_lup": bpl,
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "sums_after": {"sum_p": sums[0], "sum_ux": sums[1]},
+    }
+    if world == 1:
+        line["e2e"] = e2e_measure(torch, device, args.steps)
+        line["cpu_baseline"] = cpu_baseline_oracle()
+        if not args.quick:
+            try:
+                line["extra"] = extras(torch, device, args.quick)
+            except Exception as exc:  # keep the headline line even if a secondary row fails
+                line["extra"] = {"error": repr(exc)}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on the host cores: each step is one oracle step on a
+    one-plane (256 x 256 x 1, periodic in z) sample of the channel workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+
+    import oracle
+    import synth
+
+    shape = (1, 256, 256)
+    M0, solid = synth.channel(shape, 1e-3, seed=1)
+    lat = oracle.D3Q19
+    F = oracle.lbm.as_field((1e-6, 0.0, 0.0), shape)
+    rho = oracle.lbm.as_scalar_field(1.0, shape)
+    om = oracle.lbm.as_scalar_field(oracle.lbm.omega_from_tau(0.9), shape)
+    f = oracle.lbm.populations_from_moments(lat, M0, F, rho)
+    for _ in range(args.warmup):
+        f = oracle.lbm.step(lat, f, F, rho, om, solid)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.lbm.step(lat, f, F, rho, om, solid)
+    t = time.perf_counter() - t0
+    n = shape[0] * shape[1] * shape[2]
+    value = n * args.steps / t / 1e6
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "MLUPS", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "D3Q19", "shape_xyz": [256, 256, 256], "storage": "f64",
+                   "sample": "one 256x256 plane per step (periodic in z)"},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} FP64 population-form steps on a 256x256x1 slab of the channel"},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--quick", action="store_true", help="headline only: skip the secondary rows")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

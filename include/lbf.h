@@ -1,0 +1,155 @@
+/*
+ * lbf.h - C ABI of a single-GPU (GB300, sm_103a) moment-represented lattice Boltzmann solver.
+ *
+ * The method (arXiv 2609.09160, Sec. 2): each lattice site stores only the Hermite coefficients
+ * of the populations up to second order - the rescaled pressure p*, the velocity u and the
+ * symmetric second-order tensor a2 (10 numbers) - and one time step is the fused pull update of
+ * Eq. (pullLLB): every site rebuilds the regularized post-collision populations of its Q
+ * neighbours (Eqs. reqtfeq, hermite_teq) including the Guo source (Eq. guoforce), streams them
+ * in and takes their moments, followed by the half-force correction of Eq. (corr). D3Q19 and
+ * D3Q27 with second-order truncation are supported. The conservative Allen-Cahn phase field of
+ * Eq. (ACeq) with the capillary force provides the two-component coupling at equal densities.
+ *
+ * Conventions shared by every call
+ *  - Sites are indexed (z, y, x) with x fastest; a field is nz*ny*nx contiguous values.
+ *  - Public moment layout ("public state"): 10 fields [p*, ux, uy, uz, Axx, Ayy, Azz, Axy, Axz,
+ *    Ayz] of nz*ny*nx values each, A = a2 the total second coefficient of Eq. (corr). This is the
+ *    layout of lbf_set_moments / lbf_moments and of the adjoint cotangents.
+ *  - Internal state ("state buffer"): the same 10 fields in the storage dtype, with the tensor
+ *    stored as N = A - u u and, for 16-bit storage, every group multiplied by a power of two.
+ *    Callers treat it as opaque bytes of size lbf_state_bytes().
+ *  - Every call is ordered on the context's CUDA stream (lbf_params.stream) and returns without
+ *    waiting for the GPU, except lbf_reduce and lbf_synchronize, which wait for the stream.
+ *  - The library allocates no device memory: the caller provides one workspace of
+ *    lbf_workspace_bytes() bytes (256-byte aligned) that the context uses until lbf_destroy.
+ *  - Errors are returned as lbf_status codes; nothing aborts and no kernel traps. The message of
+ *    the last error on the calling thread is available from lbf_last_error().
+ *  - Boundaries: every axis is periodic; sites flagged solid in the mask are walls with halfway
+ *    bounce-back (the paper only states "no-slip walls"). Solid sites keep their moments.
+ */
+#ifndef LBF_H
+#define LBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbf_ctx lbf_ctx; /* opaque, host-side; owns no device memory */
+
+enum { LBF_D3Q19 = 19, LBF_D3Q27 = 27 };
+
+/* storage / transfer dtypes; F64 storage computes in FP64, every other storage in FP32 */
+enum { LBF_F64 = 0, LBF_F32 = 1, LBF_F16 = 2, LBF_BF16 = 3 };
+
+typedef enum {
+  LBF_OK = 0,
+  LBF_EINVAL = 1,      /* bad argument: sizes, tau <= 0.5, null pointer, unsupported combination */
+  LBF_ENOMEM = 2,      /* workspace too small or misaligned */
+  LBF_ECUDA = 3,       /* a CUDA runtime call failed; see lbf_last_error() */
+  LBF_EUNSTABLE = 4,   /* a step produced a non-finite value or |u| > 0.4 */
+  LBF_EINTERNAL = 5,   /* broken internal invariant */
+  LBF_ENOTSUP = 6      /* a feature the library does not build (see lbf_last_error()) */
+} lbf_status;
+
+typedef struct {
+  int lattice;          /* LBF_D3Q19 or LBF_D3Q27 */
+  int nx, ny, nz;       /* >= 1 each */
+  int storage;          /* LBF_F64, LBF_F32, LBF_F16 or LBF_BF16 */
+  double tau;           /* single-component relaxation time, > 0.5; nu = (tau - 1/2)/3
+                           (text under Eq. pullLB). Ignored when two_component != 0. */
+  double force[3];      /* uniform body force per unit volume, F^b of Sec. 2 */
+  const void* force_field; /* optional DEVICE pointer, [3][nz][ny][nx], FP64 when storage is
+                           LBF_F64 else FP32; added to force[]; borrowed: must stay valid and may
+                           be rewritten by the caller between steps; NULL = none. */
+  const uint8_t* mask;  /* optional HOST pointer, nz*ny*nx bytes, nonzero = solid; copied by
+                           lbf_create; NULL = all fluid. */
+  int two_component;    /* nonzero: conservative Allen-Cahn phase field coupled through the
+                           capillary force (Eq. ACeq, F^s = mu grad phi); requires mask == NULL
+                           and rho_l == rho_h (the pressure and viscous-gradient forces of the
+                           paper vanish there and are not built). */
+  double rho_l, rho_h;  /* densities of the light (phi = 0) and heavy (phi = 1) phase */
+  double tau_l, tau_h;  /* relaxation times; nu(phi) = nu_l + phi (nu_h - nu_l) */
+  double sigma, width;  /* surface tension and interface width W: beta = 12 sigma/W,
+                           kappa = 3 sigma W / 2, lambda = 4 D / W */
+  double diffusivity;   /* interface diffusivity D of Eq. (ACeq) */
+  double scale_hint[3]; /* 16-bit storage: expected max |p*|, |u|, |A - u u|; 0 = take each from
+                           the state given to lbf_set_moments */
+  void* stream;         /* cudaStream_t used for every call; NULL = legacy default stream */
+} lbf_params;
+
+/* Workspace bytes the context needs for these parameters, 0 if the parameters are invalid.
+   Host-only: makes no CUDA call. The moment buffers take 2 * 10 * nx*ny*nz * sizeof(storage). */
+size_t lbf_workspace_bytes(const lbf_params* params);
+
+/* Checks parameters on the host without touching the GPU. */
+lbf_status lbf_validate(const lbf_params* params);
+
+/* Creates a context on the current CUDA device. workspace: DEVICE pointer, 256-byte aligned, at
+   least lbf_workspace_bytes(params) bytes, owned by the caller and kept alive until lbf_destroy.
+   The state is zero (fluid at rest) until lbf_set_moments. */
+lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, size_t bytes);
+
+/* Loads the public state. src: 10 fields (public layout) of dtype LBF_F64 or LBF_F32, HOST or
+   DEVICE memory (detected); phi: nz*ny*nx phase-field values of the same dtype and memory kind,
+   required when two_component, else ignored. Host sources are copied through a staging area of
+   the workspace; pinned host memory makes the copies asynchronous. For 16-bit storage the
+   power-of-two scales are chosen here (unless scale_hint is set). Also computes the initial
+   phase-field force when two_component. */
+lbf_status lbf_set_moments(lbf_ctx* ctx, const void* src, int src_dtype, const void* phi);
+
+/* Advances n >= 0 time steps (one fused kernel per step; two more phase-field kernels per step
+   when two_component). The conservation sums of the final state are computed on the last step.
+   Returns LBF_EUNSTABLE if an earlier lbf_reduce/lbf_synchronize saw the instability flag. */
+lbf_status lbf_step(lbf_ctx* ctx, int n);
+
+/* Writes the public state (dst, 10 fields) and, when two_component and phi_dst != NULL, the phase
+   field, in dtype LBF_F64 or LBF_F32, to HOST or DEVICE memory (detected). Asynchronous for device
+   or pinned host destinations. */
+lbf_status lbf_moments(lbf_ctx* ctx, void* dst, int dst_dtype, void* phi_dst);
+
+/* Waits for the stream and returns FP64 [sum p*, sum ux, sum uy, sum uz, sum phi, sum u.u] over
+   fluid sites of the current state (out: HOST, 6 doubles). LBF_EUNSTABLE if any step so far saw a
+   non-finite value or |u|^2 > 0.16 (out is still filled). */
+lbf_status lbf_reduce(lbf_ctx* ctx, double* out);
+
+/* Waits for the stream; LBF_EUNSTABLE as for lbf_reduce. */
+lbf_status lbf_synchronize(lbf_ctx* ctx);
+
+/* Bytes of one internal state buffer (10 * nx*ny*nz * sizeof(storage)). */
+size_t lbf_state_bytes(const lbf_ctx* ctx);
+
+/* Copies the current internal state to / from a caller DEVICE buffer of lbf_state_bytes()
+   (checkpointing; stream-ordered). */
+lbf_status lbf_copy_state(lbf_ctx* ctx, void* dst);
+lbf_status lbf_load_state(lbf_ctx* ctx, const void* src);
+
+/* One single-component step from internal state src to internal state dst (caller DEVICE
+   buffers of lbf_state_bytes(); src != dst). The context's own state is not touched. Solid
+   sites of dst are not written. */
+lbf_status lbf_step_state(lbf_ctx* ctx, const void* src, void* dst);
+
+/* Adjoint of one single-component step (not in the paper; the discrete adjoint of the step
+   above). Given the internal states at t and t+1 (state_t, state_t1), and lambda_in = dL/dM(t+1)
+   in the public layout (10 fields, FP64 when storage is LBF_F64 else FP32, DEVICE), writes
+   lambda_out = dL/dM(t) (same layout and dtype, DEVICE, distinct from lambda_in) and adds
+   dL/dF contributed by this step to grad_force (DEVICE, FP64, [3][nz][ny][nx]) for the total
+   per-site force (uniform force + force_field). Solid sites pass lambda through unchanged and
+   get no force gradient. Not available for 16-bit storage or two_component (LBF_ENOTSUP). */
+lbf_status lbf_adjoint_step(lbf_ctx* ctx, const void* state_t, const void* state_t1, const void* lambda_in,
+                            void* lambda_out, double* grad_force);
+
+/* Releases the host-side context. The workspace stays owned by the caller. */
+lbf_status lbf_destroy(lbf_ctx* ctx);
+
+const char* lbf_status_string(int status);
+const char* lbf_last_error(void);
+int lbf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBF_H */

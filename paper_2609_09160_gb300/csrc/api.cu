@@ -1,0 +1,734 @@
+// Host side of the C ABI declared in include/lbf.h: parameter validation, workspace layout,
+// context state, stream-ordered launches and host <-> device staging.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbf.h"
+#include "aux_kernels.cuh"
+#include "dispatch.cuh"
+
+using namespace lbf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lbf_status fail(lbf_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define LBF_CUDA(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(LBF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));             \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr size_t kStagingMax = size_t(16) << 20;
+constexpr double kTarget16 = 4096.0;  // 16-bit: the largest magnitude of a group maps near 2^12
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+size_t storage_bytes(int storage) {
+  switch (storage) {
+    case LBF_F64: return 8;
+    case LBF_F32: return 4;
+    case LBF_F16:
+    case LBF_BF16: return 2;
+  }
+  return 0;
+}
+
+size_t compute_bytes(int storage) { return storage == LBF_F64 ? 8 : 4; }
+
+struct Layout {
+  size_t state[2], mask, phi[2], F[2], G, partials, scal, staging, total;
+  long long npartials;
+  size_t staging_bytes;
+};
+
+lbf_status check_params(const lbf_params* p) {
+  if (p == nullptr) return fail(LBF_EINVAL, "params is NULL");
+  if (p->lattice != LBF_D3Q19 && p->lattice != LBF_D3Q27) return fail(LBF_EINVAL, "lattice must be 19 or 27");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LBF_EINVAL, "nx, ny, nz must be >= 1");
+  const double n = double(p->nx) * double(p->ny) * double(p->nz);
+  if (n > 4.0e10) return fail(LBF_EINVAL, "lattice too large");
+  if (storage_bytes(p->storage) == 0) return fail(LBF_EINVAL, "storage must be LBF_F64, LBF_F32, LBF_F16 or LBF_BF16");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(p->force[a])) return fail(LBF_EINVAL, "force must be finite");
+  if (p->two_component) {
+    if (!(p->tau_l > 0.5) || !(p->tau_h > 0.5)) return fail(LBF_EINVAL, "tau_l and tau_h must be > 0.5");
+    if (!(p->rho_l > 0.0) || !(p->rho_h > 0.0)) return fail(LBF_EINVAL, "rho_l and rho_h must be > 0");
+    if (p->rho_l != p->rho_h)
+      return fail(LBF_ENOTSUP,
+                  "two-component with a density contrast needs the pressure and viscous-gradient forces, which are not built");
+    if (p->mask != nullptr) return fail(LBF_ENOTSUP, "two-component with walls (no wetting condition) is not built");
+    if (!(p->width > 0.0) || !(p->sigma >= 0.0) || !(p->diffusivity >= 0.0))
+      return fail(LBF_EINVAL, "need width > 0, sigma >= 0, diffusivity >= 0");
+    if (p->force_field != nullptr) return fail(LBF_ENOTSUP, "two-component with a force field is not built");
+  } else {
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(LBF_EINVAL, "tau must be > 0.5");
+  }
+  return LBF_OK;
+}
+
+int grid_x(int nx) { return (nx + FwdTile<8>::XOUT - 1) / FwdTile<8>::XOUT; }
+int grid_y(int ny, int storage) { const int by = tile_rows(storage); return (ny + by - 1) / by; }
+int min_zchunk(int nz) { return std::min(8, nz); }
+
+bool make_layout(const lbf_params* p, Layout* L) {
+  if (check_params(p) != LBF_OK) return false;
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  const size_t sb = storage_bytes(p->storage), cb = compute_bytes(p->storage);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  L->state[0] = take(10 * N * sb);
+  L->state[1] = take(10 * N * sb);
+  L->mask = p->mask ? take(N) : 0;
+  if (p->two_component) {
+    L->phi[0] = take(N * cb);
+    L->phi[1] = take(N * cb);
+    L->F[0] = take(3 * N * cb);
+    L->F[1] = take(3 * N * cb);
+    L->G = take(3 * N * cb);
+  } else {
+    L->phi[0] = L->phi[1] = L->F[0] = L->F[1] = L->G = 0;
+  }
+  const long long gz = (p->nz + min_zchunk(p->nz) - 1) / min_zchunk(p->nz);
+  L->npartials = std::max<long long>((long long)grid_x(p->nx) * grid_y(p->ny, p->storage) * gz, 1024);
+  L->partials = take(size_t(L->npartials) * 8 * sizeof(double));
+  L->scal = take(64 * sizeof(double));
+  L->staging_bytes = std::min<size_t>(kStagingMax, size_t(11) * 8 * size_t(N));
+  L->staging = take(L->staging_bytes);
+  L->total = off;
+  return true;
+}
+
+float pow2f(int s) { return std::ldexp(1.0f, s); }
+
+int choose_shift(double maxabs, double fallback) {
+  const double m = maxabs > 0.0 && std::isfinite(maxabs) ? maxabs : fallback;
+  int s = (int)std::floor(std::log2(kTarget16 / m));
+  return std::max(-30, std::min(60, s));
+}
+
+}  // namespace
+
+struct lbf_ctx {
+  lbf_params prm;
+  Layout lay;
+  int Q, storage;
+  bool has_mask, two;
+  int nx, ny, nz;
+  long long N;
+  unsigned char* ws;
+  void* state[2];
+  int cur;
+  uint8_t* mask_d;
+  void* phi[2];
+  void* F[2];
+  void* G;
+  int pcur;
+  double* partials;
+  double* sums;       // 8 doubles at scal
+  unsigned* flags;    // after sums
+  unsigned* absmax;   // 3 words
+  unsigned* counter;  // blocks done in the fused reduction
+  unsigned char* staging;
+  Scales sc;
+  cudaStream_t stream;
+  int zchunk;
+  dim3 fgrid;
+  KernelInfo fwd, adj;
+  bool sums_valid;
+  bool unstable_seen;
+  double omega, nu_l, nu_h;
+};
+
+namespace {
+
+KernelInfo forward_for(int Q, int storage, bool mask, bool two) {
+  return Q == 19 ? forward_kernel_q19(storage, mask, two) : forward_kernel_q27(storage, mask, two);
+}
+KernelInfo adjoint_for(int Q, int storage, bool mask) {
+  return Q == 19 ? adjoint_kernel_q19(storage, mask) : adjoint_kernel_q27(storage, mask);
+}
+
+lbf_status prepare(const KernelInfo& k) {
+  if (k.fn == nullptr) return LBF_OK;
+  LBF_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+  return LBF_OK;
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+unsigned blocks_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (unsigned)std::max<long long>(1, std::min<long long>(b, 65535LL * 16));
+}
+
+template <class Tin, class S>
+void launch_encode(const void* src, long long stride, long long site0, long long count, void* dst, long long N, Scales sc,
+                   cudaStream_t st) {
+  k_encode<Tin, S><<<blocks_for(count, 256), 256, 0, st>>>(static_cast<const Tin*>(src), stride, site0, count,
+                                                           static_cast<S*>(dst), N, sc);
+}
+
+template <class Tin>
+void encode_dispatch(int storage, const void* src, long long stride, long long site0, long long count, void* dst,
+                     long long N, Scales sc, cudaStream_t st) {
+  switch (storage) {
+    case LBF_F64: launch_encode<Tin, double>(src, stride, site0, count, dst, N, sc, st); break;
+    case LBF_F32: launch_encode<Tin, float>(src, stride, site0, count, dst, N, sc, st); break;
+    case LBF_F16: launch_encode<Tin, __half>(src, stride, site0, count, dst, N, sc, st); break;
+    case LBF_BF16: launch_encode<Tin, __nv_bfloat16>(src, stride, site0, count, dst, N, sc, st); break;
+  }
+}
+
+template <class S, class Tout>
+void launch_decode(const void* src, long long N, long long site0, long long count, void* dst, long long stride, Scales sc,
+                   cudaStream_t st) {
+  k_decode<S, Tout><<<blocks_for(count, 256), 256, 0, st>>>(static_cast<const S*>(src), N, site0, count,
+                                                            static_cast<Tout*>(dst), stride, sc);
+}
+
+template <class Tout>
+void decode_dispatch(int storage, const void* src, long long N, long long site0, long long count, void* dst,
+                     long long stride, Scales sc, cudaStream_t st) {
+  switch (storage) {
+    case LBF_F64: launch_decode<double, Tout>(src, N, site0, count, dst, stride, sc, st); break;
+    case LBF_F32: launch_decode<float, Tout>(src, N, site0, count, dst, stride, sc, st); break;
+    case LBF_F16: launch_decode<__half, Tout>(src, N, site0, count, dst, stride, sc, st); break;
+    case LBF_BF16: launch_decode<__nv_bfloat16, Tout>(src, N, site0, count, dst, stride, sc, st); break;
+  }
+}
+
+template <class Tin, class Tout>
+__global__ void k_convert(const Tin* __restrict__ a, Tout* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = static_cast<Tout>(a[i]);
+}
+
+void convert(const void* a, int da, void* b, int db, long long n, cudaStream_t st) {
+  const unsigned g = blocks_for(n, 256);
+  if (da == LBF_F64 && db == LBF_F64) k_convert<double, double><<<g, 256, 0, st>>>((const double*)a, (double*)b, n);
+  else if (da == LBF_F64) k_convert<double, float><<<g, 256, 0, st>>>((const double*)a, (float*)b, n);
+  else if (db == LBF_F64) k_convert<float, double><<<g, 256, 0, st>>>((const float*)a, (double*)b, n);
+  else k_convert<float, float><<<g, 256, 0, st>>>((const float*)a, (float*)b, n);
+}
+
+PhaseParams phase_params(const lbf_ctx* c) {
+  PhaseParams pp;
+  pp.nx = c->nx;
+  pp.ny = c->ny;
+  pp.nz = c->nz;
+  pp.N = c->N;
+  pp.D = c->prm.diffusivity;
+  pp.lambda = 4.0 * c->prm.diffusivity / c->prm.width;
+  pp.beta = 12.0 * c->prm.sigma / c->prm.width;
+  pp.kappa = 1.5 * c->prm.sigma * c->prm.width;
+  for (int a = 0; a < 3; ++a) pp.body[a] = c->prm.force[a];
+  pp.sc = c->sc;
+  return pp;
+}
+
+dim3 phase_block() { return dim3(32, 4, 2); }
+dim3 phase_grid(const lbf_ctx* c) {
+  const dim3 b = phase_block();
+  return dim3((c->nx + b.x - 1) / b.x, (c->ny + b.y - 1) / b.y, (c->nz + b.z - 1) / b.z);
+}
+
+template <class T>
+void launch_forces_T(lbf_ctx* c, int which) {
+  k_phase_forces<T><<<phase_grid(c), phase_block(), 0, c->stream>>>(static_cast<const T*>(c->phi[which]),
+                                                                     static_cast<T*>(c->F[which]),
+                                                                     static_cast<T*>(c->G), phase_params(c));
+}
+
+void launch_forces(lbf_ctx* c, int which) {
+  if (c->storage == LBF_F64) launch_forces_T<double>(c, which);
+  else launch_forces_T<float>(c, which);
+}
+
+template <class S, class T>
+void launch_advance_T(lbf_ctx* c) {
+  k_phase_advance<S, T><<<phase_grid(c), phase_block(), 0, c->stream>>>(
+      static_cast<const S*>(c->state[c->cur]), static_cast<const T*>(c->phi[c->pcur]), static_cast<const T*>(c->G),
+      static_cast<T*>(c->phi[1 - c->pcur]), phase_params(c));
+}
+
+void launch_advance(lbf_ctx* c) {
+  switch (c->storage) {
+    case LBF_F64: launch_advance_T<double, double>(c); break;
+    case LBF_F32: launch_advance_T<float, float>(c); break;
+    case LBF_F16: launch_advance_T<__half, float>(c); break;
+    case LBF_BF16: launch_advance_T<__nv_bfloat16, float>(c); break;
+  }
+}
+
+FwdParams forward_params(const lbf_ctx* c, const void* src, void* dst, bool reduce) {
+  FwdParams a;
+  std::memset(&a, 0, sizeof(a));
+  a.src = src;
+  a.dst = dst;
+  a.mask = c->mask_d;
+  a.force_field = c->prm.force_field;
+  for (int k = 0; k < 3; ++k) a.force[k] = c->prm.force[k];
+  a.omega = c->omega;
+  if (c->two) {
+    a.phi_old = c->phi[c->pcur];
+    a.phi_new = c->phi[1 - c->pcur];
+    a.F_old = c->F[c->pcur];
+    a.F_new = c->F[1 - c->pcur];
+    a.rho_l = c->prm.rho_l;
+    a.rho_h = c->prm.rho_h;
+    a.nu_l = c->nu_l;
+    a.nu_h = c->nu_h;
+  }
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.N = c->N;
+  a.sc = c->sc;
+  a.partials = reduce ? c->partials : nullptr;
+  a.sums = c->sums;
+  a.counter = c->counter;
+  a.flags = c->flags;
+  a.zchunk = c->zchunk;
+  a.umax2 = 0.16f;
+  return a;
+}
+
+lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
+  FwdParams a = forward_params(c, src, dst, reduce);
+  void* args[] = {&a};
+  LBF_CUDA(cudaLaunchKernel(c->fwd.fn, c->fgrid, dim3(32, c->fwd.by + 2, 1), args, c->fwd.smem, c->stream));
+  return LBF_OK;
+}
+
+long long forward_blocks(const lbf_ctx* c) { return (long long)c->fgrid.x * c->fgrid.y * c->fgrid.z; }
+
+lbf_status finalize_sums(lbf_ctx* c, long long nblocks) {
+  k_reduce_final<<<1, 256, 0, c->stream>>>(c->partials, nblocks, c->sums);
+  LBF_CUDA(cudaGetLastError());
+  c->sums_valid = true;
+  return LBF_OK;
+}
+
+template <class S>
+void launch_reduce_state_T(lbf_ctx* c, unsigned grid) {
+  k_reduce_state<S><<<grid, 256, 0, c->stream>>>(static_cast<const S*>(c->state[c->cur]), c->N, c->mask_d,
+                                                   c->two ? c->phi[c->pcur] : nullptr, c->storage == LBF_F64, c->sc,
+                                                   c->partials);
+}
+
+lbf_status reduce_state(lbf_ctx* c) {
+  const unsigned grid = (unsigned)std::min<long long>(1024, std::max<long long>(1, (c->N + 255) / 256));
+  switch (c->storage) {
+    case LBF_F64: launch_reduce_state_T<double>(c, grid); break;
+    case LBF_F32: launch_reduce_state_T<float>(c, grid); break;
+    case LBF_F16: launch_reduce_state_T<__half>(c, grid); break;
+    case LBF_BF16: launch_reduce_state_T<__nv_bfloat16>(c, grid); break;
+  }
+  LBF_CUDA(cudaGetLastError());
+  return finalize_sums(c, grid);
+}
+
+void set_scales(lbf_ctx* c, const double m[3]) {
+  const double fallback[3] = {1e-3, 0.1, 1e-3};
+  for (int g = 0; g < 3; ++g) {
+    if (c->storage == LBF_F16 || c->storage == LBF_BF16) {
+      const double hint = c->prm.scale_hint[g];
+      const int s = choose_shift(hint > 0.0 ? hint : m[g], fallback[g]);
+      c->sc.enc[g] = pow2f(s);
+      c->sc.dec[g] = pow2f(-s);
+    } else {
+      c->sc.enc[g] = 1.0f;
+      c->sc.dec[g] = 1.0f;
+    }
+  }
+}
+
+template <class T>
+void host_absmax(const T* src, long long N, double m[3]) {
+  m[0] = m[1] = m[2] = 0.0;
+  for (long long i = 0; i < N; ++i) {
+    const double p = src[i], ux = src[N + i], uy = src[2 * N + i], uz = src[3 * N + i];
+    m[0] = std::max(m[0], std::fabs(p));
+    m[1] = std::max(m[1], std::max(std::fabs(ux), std::max(std::fabs(uy), std::fabs(uz))));
+    const double n[6] = {src[4 * N + i] - ux * ux, src[5 * N + i] - uy * uy, src[6 * N + i] - uz * uz,
+                         src[7 * N + i] - ux * uy, src[8 * N + i] - ux * uz, src[9 * N + i] - uy * uz};
+    for (int k = 0; k < 6; ++k) m[2] = std::max(m[2], std::fabs(n[k]));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbf_version(void) { return 1; }
+
+const char* lbf_last_error(void) { return g_last_error.c_str(); }
+
+const char* lbf_status_string(int s) {
+  switch (s) {
+    case LBF_OK: return "LBF_OK";
+    case LBF_EINVAL: return "LBF_EINVAL";
+    case LBF_ENOMEM: return "LBF_ENOMEM";
+    case LBF_ECUDA: return "LBF_ECUDA";
+    case LBF_EUNSTABLE: return "LBF_EUNSTABLE";
+    case LBF_EINTERNAL: return "LBF_EINTERNAL";
+    case LBF_ENOTSUP: return "LBF_ENOTSUP";
+  }
+  return "LBF_UNKNOWN";
+}
+
+lbf_status lbf_validate(const lbf_params* params) { return check_params(params); }
+
+size_t lbf_workspace_bytes(const lbf_params* params) {
+  Layout L;
+  if (!make_layout(params, &L)) return 0;
+  return L.total;
+}
+
+lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, size_t bytes) {
+  if (out == nullptr) return fail(LBF_EINVAL, "out is NULL");
+  *out = nullptr;
+  lbf_status st = check_params(params);
+  if (st != LBF_OK) return st;
+  Layout L;
+  make_layout(params, &L);
+  if (workspace == nullptr) return fail(LBF_EINVAL, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign != 0) return fail(LBF_ENOMEM, "workspace must be 256-byte aligned");
+  if (bytes < L.total)
+    return fail(LBF_ENOMEM, "workspace too small: need " + std::to_string(L.total) + " bytes");
+  lbf_ctx* c = new lbf_ctx();
+  c->prm = *params;
+  c->prm.mask = nullptr;  // host mask is copied, never kept
+  c->lay = L;
+  c->Q = params->lattice;
+  c->storage = params->storage;
+  c->has_mask = params->mask != nullptr;
+  c->two = params->two_component != 0;
+  c->nx = params->nx;
+  c->ny = params->ny;
+  c->nz = params->nz;
+  c->N = (long long)c->nx * c->ny * c->nz;
+  c->ws = static_cast<unsigned char*>(workspace);
+  c->state[0] = c->ws + L.state[0];
+  c->state[1] = c->ws + L.state[1];
+  c->cur = 0;
+  c->mask_d = c->has_mask ? reinterpret_cast<uint8_t*>(c->ws + L.mask) : nullptr;
+  for (int k = 0; k < 2; ++k) {
+    c->phi[k] = c->two ? c->ws + L.phi[k] : nullptr;
+    c->F[k] = c->two ? c->ws + L.F[k] : nullptr;
+  }
+  c->G = c->two ? c->ws + L.G : nullptr;
+  c->pcur = 0;
+  c->partials = reinterpret_cast<double*>(c->ws + L.partials);
+  c->sums = reinterpret_cast<double*>(c->ws + L.scal);
+  c->flags = reinterpret_cast<unsigned*>(c->sums + 8);
+  c->absmax = c->flags + 4;
+  c->counter = c->flags + 8;
+  c->staging = c->ws + L.staging;
+  c->stream = static_cast<cudaStream_t>(params->stream);
+  c->omega = 1.0 / params->tau;
+  c->nu_l = (params->tau_l - 0.5) / 3.0;
+  c->nu_h = (params->tau_h - 0.5) / 3.0;
+  c->sums_valid = false;
+  c->unstable_seen = false;
+  const double m0[3] = {0.0, 0.0, 0.0};
+  set_scales(c, m0);
+
+  c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two);
+  c->adj = adjoint_for(c->Q, c->storage, c->has_mask);
+  if (c->fwd.fn == nullptr) {
+    delete c;
+    return fail(LBF_ENOTSUP, "no kernel for this combination");
+  }
+  auto cleanup = [&](lbf_status s) {
+    delete c;
+    return s;
+  };
+  if ((st = prepare(c->fwd)) != LBF_OK) return cleanup(st);
+  if ((st = prepare(c->adj)) != LBF_OK) return cleanup(st);
+
+  // z-chunk: enough CTAs for about two waves of resident blocks, at least 8 planes per chunk
+  int dev = 0, sms = 1, per_sm = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c->fwd.fn, c->fwd.threads, c->fwd.smem) != cudaSuccess)
+    return cleanup(fail(LBF_ECUDA, std::string("device query failed: ") + cudaGetErrorString(cudaGetLastError())));
+  per_sm = std::max(per_sm, 1);
+  const long long tiles = (long long)grid_x(c->nx) * grid_y(c->ny, c->storage);
+  const long long want = 2LL * sms * per_sm;
+  long long chunks = std::max<long long>(1, (want + tiles - 1) / tiles);
+  int zc = (int)std::max<long long>(min_zchunk(c->nz), (c->nz + chunks - 1) / chunks);
+  if (const char* e = std::getenv("LBF_ZCHUNK")) {
+    const int v = std::atoi(e);
+    if (v >= 1) zc = std::max(min_zchunk(c->nz), v);
+  }
+  c->zchunk = std::min(zc, c->nz);
+  c->fgrid = dim3(grid_x(c->nx), grid_y(c->ny, c->storage), (c->nz + c->zchunk - 1) / c->zchunk);
+  if (forward_blocks(c) > L.npartials) return cleanup(fail(LBF_EINTERNAL, "partials buffer too small"));
+
+  cudaStream_t s = c->stream;
+  if (cudaMemsetAsync(c->state[0], 0, 10 * c->N * storage_bytes(c->storage), s) != cudaSuccess ||
+      cudaMemsetAsync(c->state[1], 0, 10 * c->N * storage_bytes(c->storage), s) != cudaSuccess ||
+      cudaMemsetAsync(c->sums, 0, 64 * sizeof(double), s) != cudaSuccess)
+    return cleanup(fail(LBF_ECUDA, "memset failed"));
+  if (c->has_mask) {
+    if (cudaMemcpyAsync(c->mask_d, params->mask, c->N, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return cleanup(fail(LBF_ECUDA, "mask copy failed"));
+  }
+  if (c->two) {
+    const size_t cb = compute_bytes(c->storage);
+    for (int k = 0; k < 2; ++k) {
+      if (cudaMemsetAsync(c->phi[k], 0, c->N * cb, s) != cudaSuccess ||
+          cudaMemsetAsync(c->F[k], 0, 3 * c->N * cb, s) != cudaSuccess)
+        return cleanup(fail(LBF_ECUDA, "memset failed"));
+    }
+    if (cudaMemsetAsync(c->G, 0, 3 * c->N * cb, s) != cudaSuccess) return cleanup(fail(LBF_ECUDA, "memset failed"));
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess)
+    return cleanup(fail(LBF_ECUDA, std::string("create: ") + cudaGetErrorString(cudaGetLastError())));
+  *out = c;
+  return LBF_OK;
+}
+
+lbf_status lbf_destroy(lbf_ctx* c) {
+  delete c;
+  return LBF_OK;
+}
+
+size_t lbf_state_bytes(const lbf_ctx* c) { return c ? size_t(10) * c->N * storage_bytes(c->storage) : 0; }
+
+lbf_status lbf_set_moments(lbf_ctx* c, const void* src, int dt, const void* phi) {
+  if (c == nullptr || src == nullptr) return fail(LBF_EINVAL, "NULL argument");
+  if (dt != LBF_F64 && dt != LBF_F32) return fail(LBF_EINVAL, "src_dtype must be LBF_F64 or LBF_F32");
+  if (c->two && phi == nullptr) return fail(LBF_EINVAL, "two-component state needs phi");
+  const bool dev = is_device_pointer(src);
+  const size_t eb = dt == LBF_F64 ? 8 : 4;
+  const long long N = c->N;
+  cudaStream_t s = c->stream;
+  if (c->storage == LBF_F16 || c->storage == LBF_BF16) {
+    double m[3] = {0, 0, 0};
+    if (dev) {
+      LBF_CUDA(cudaMemsetAsync(c->absmax, 0, 3 * sizeof(unsigned), s));
+      if (dt == LBF_F64)
+        k_absmax<double><<<blocks_for(N, 256), 256, 0, s>>>(static_cast<const double*>(src), N, N, c->absmax);
+      else
+        k_absmax<float><<<blocks_for(N, 256), 256, 0, s>>>(static_cast<const float*>(src), N, N, c->absmax);
+      LBF_CUDA(cudaGetLastError());
+      unsigned h[3];
+      LBF_CUDA(cudaMemcpyAsync(h, c->absmax, sizeof(h), cudaMemcpyDeviceToHost, s));
+      LBF_CUDA(cudaStreamSynchronize(s));
+      for (int k = 0; k < 3; ++k) {
+        float f;
+        std::memcpy(&f, &h[k], sizeof(f));
+        m[k] = f;
+      }
+    } else if (dt == LBF_F64) {
+      host_absmax(static_cast<const double*>(src), N, m);
+    } else {
+      host_absmax(static_cast<const float*>(src), N, m);
+    }
+    set_scales(c, m);
+  }
+  if (dev) {
+    if (dt == LBF_F64) encode_dispatch<double>(c->storage, src, N, 0, N, c->state[0], N, c->sc, s);
+    else encode_dispatch<float>(c->storage, src, N, 0, N, c->state[0], N, c->sc, s);
+    LBF_CUDA(cudaGetLastError());
+  } else {
+    const long long chunk = std::max<long long>(1, (long long)(c->lay.staging_bytes / (10 * eb)));
+    const unsigned char* h = static_cast<const unsigned char*>(src);
+    for (long long s0 = 0; s0 < N; s0 += chunk) {
+      const long long cnt = std::min(chunk, N - s0);
+      for (int k = 0; k < 10; ++k)
+        LBF_CUDA(cudaMemcpyAsync(c->staging + k * cnt * eb, h + (k * N + s0) * eb, cnt * eb, cudaMemcpyHostToDevice, s));
+      if (dt == LBF_F64) encode_dispatch<double>(c->storage, c->staging, cnt, s0, cnt, c->state[0], N, c->sc, s);
+      else encode_dispatch<float>(c->storage, c->staging, cnt, s0, cnt, c->state[0], N, c->sc, s);
+      LBF_CUDA(cudaGetLastError());
+    }
+  }
+  LBF_CUDA(cudaMemcpyAsync(c->state[1], c->state[0], lbf_state_bytes(c), cudaMemcpyDeviceToDevice, s));
+  c->cur = 0;
+  c->pcur = 0;
+  if (c->two) {
+    const int cd = c->storage == LBF_F64 ? LBF_F64 : LBF_F32;
+    const bool pdev = is_device_pointer(phi);
+    if (pdev) {
+      convert(phi, dt, c->phi[0], cd, N, s);
+      LBF_CUDA(cudaGetLastError());
+    } else {
+      const long long chunk = std::max<long long>(1, (long long)(c->lay.staging_bytes / eb));
+      const unsigned char* h = static_cast<const unsigned char*>(phi);
+      const size_t cbytes = compute_bytes(c->storage);
+      for (long long s0 = 0; s0 < N; s0 += chunk) {
+        const long long cnt = std::min(chunk, N - s0);
+        LBF_CUDA(cudaMemcpyAsync(c->staging, h + s0 * eb, cnt * eb, cudaMemcpyHostToDevice, s));
+        convert(c->staging, dt, static_cast<unsigned char*>(c->phi[0]) + s0 * cbytes, cd, cnt, s);
+        LBF_CUDA(cudaGetLastError());
+      }
+    }
+    launch_forces(c, 0);
+    LBF_CUDA(cudaGetLastError());
+  }
+  c->sums_valid = false;
+  return LBF_OK;
+}
+
+lbf_status lbf_step(lbf_ctx* c, int n) {
+  if (c == nullptr || n < 0) return fail(LBF_EINVAL, "bad argument");
+  for (int i = 0; i < n; ++i) {
+    const bool last = i == n - 1;
+    if (c->two) {
+      launch_advance(c);
+      LBF_CUDA(cudaGetLastError());
+      launch_forces(c, 1 - c->pcur);
+      LBF_CUDA(cudaGetLastError());
+    }
+    lbf_status st = launch_forward(c, c->state[c->cur], c->state[1 - c->cur], last);
+    if (st != LBF_OK) return st;
+    c->cur ^= 1;
+    if (c->two) c->pcur ^= 1;
+  }
+  if (n > 0) c->sums_valid = true;  // the last step's kernel wrote them
+  return c->unstable_seen ? fail(LBF_EUNSTABLE, "instability flagged by an earlier step") : LBF_OK;
+}
+
+lbf_status lbf_step_state(lbf_ctx* c, const void* src, void* dst) {
+  if (c == nullptr || src == nullptr || dst == nullptr || src == dst) return fail(LBF_EINVAL, "bad argument");
+  if (c->two) return fail(LBF_ENOTSUP, "lbf_step_state is single-component only");
+  return launch_forward(c, src, dst, false);
+}
+
+lbf_status lbf_moments(lbf_ctx* c, void* dst, int dt, void* phi_dst) {
+  if (c == nullptr || dst == nullptr) return fail(LBF_EINVAL, "NULL argument");
+  if (dt != LBF_F64 && dt != LBF_F32) return fail(LBF_EINVAL, "dst_dtype must be LBF_F64 or LBF_F32");
+  const long long N = c->N;
+  const size_t eb = dt == LBF_F64 ? 8 : 4;
+  cudaStream_t s = c->stream;
+  const void* st = c->state[c->cur];
+  if (is_device_pointer(dst)) {
+    if (dt == LBF_F64) decode_dispatch<double>(c->storage, st, N, 0, N, dst, N, c->sc, s);
+    else decode_dispatch<float>(c->storage, st, N, 0, N, dst, N, c->sc, s);
+    LBF_CUDA(cudaGetLastError());
+  } else {
+    const long long chunk = std::max<long long>(1, (long long)(c->lay.staging_bytes / (10 * eb)));
+    unsigned char* h = static_cast<unsigned char*>(dst);
+    for (long long s0 = 0; s0 < N; s0 += chunk) {
+      const long long cnt = std::min(chunk, N - s0);
+      if (dt == LBF_F64) decode_dispatch<double>(c->storage, st, N, s0, cnt, c->staging, cnt, c->sc, s);
+      else decode_dispatch<float>(c->storage, st, N, s0, cnt, c->staging, cnt, c->sc, s);
+      LBF_CUDA(cudaGetLastError());
+      for (int k = 0; k < 10; ++k)
+        LBF_CUDA(cudaMemcpyAsync(h + (k * N + s0) * eb, c->staging + k * cnt * eb, cnt * eb, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  if (c->two && phi_dst != nullptr) {
+    const int cd = c->storage == LBF_F64 ? LBF_F64 : LBF_F32;
+    if (is_device_pointer(phi_dst)) {
+      convert(c->phi[c->pcur], cd, phi_dst, dt, N, s);
+      LBF_CUDA(cudaGetLastError());
+    } else {
+      const long long chunk = std::max<long long>(1, (long long)(c->lay.staging_bytes / eb));
+      const size_t cbytes = compute_bytes(c->storage);
+      unsigned char* h = static_cast<unsigned char*>(phi_dst);
+      for (long long s0 = 0; s0 < N; s0 += chunk) {
+        const long long cnt = std::min(chunk, N - s0);
+        convert(static_cast<unsigned char*>(c->phi[c->pcur]) + s0 * cbytes, cd, c->staging, dt, cnt, s);
+        LBF_CUDA(cudaGetLastError());
+        LBF_CUDA(cudaMemcpyAsync(h + s0 * eb, c->staging, cnt * eb, cudaMemcpyDeviceToHost, s));
+      }
+    }
+  }
+  return LBF_OK;
+}
+
+lbf_status lbf_synchronize(lbf_ctx* c) {
+  if (c == nullptr) return fail(LBF_EINVAL, "NULL context");
+  unsigned f = 0;
+  LBF_CUDA(cudaMemcpyAsync(&f, c->flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
+  LBF_CUDA(cudaStreamSynchronize(c->stream));
+  if (f & 1u) c->unstable_seen = true;
+  return c->unstable_seen ? fail(LBF_EUNSTABLE, "non-finite value or |u| > 0.4 in a step") : LBF_OK;
+}
+
+lbf_status lbf_reduce(lbf_ctx* c, double* out) {
+  if (c == nullptr || out == nullptr) return fail(LBF_EINVAL, "NULL argument");
+  if (!c->sums_valid) {
+    lbf_status st = reduce_state(c);
+    if (st != LBF_OK) return st;
+  }
+  double h[6];
+  LBF_CUDA(cudaMemcpyAsync(h, c->sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  lbf_status st = lbf_synchronize(c);
+  std::memcpy(out, h, sizeof(h));
+  return st;
+}
+
+lbf_status lbf_copy_state(lbf_ctx* c, void* dst) {
+  if (c == nullptr || dst == nullptr) return fail(LBF_EINVAL, "NULL argument");
+  LBF_CUDA(cudaMemcpyAsync(dst, c->state[c->cur], lbf_state_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+  return LBF_OK;
+}
+
+lbf_status lbf_load_state(lbf_ctx* c, const void* src) {
+  if (c == nullptr || src == nullptr) return fail(LBF_EINVAL, "NULL argument");
+  LBF_CUDA(cudaMemcpyAsync(c->state[c->cur], src, lbf_state_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+  LBF_CUDA(cudaMemcpyAsync(c->state[1 - c->cur], src, lbf_state_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+  c->sums_valid = false;
+  return LBF_OK;
+}
+
+lbf_status lbf_adjoint_step(lbf_ctx* c, const void* state_t, const void* state_t1, const void* lambda_in,
+                            void* lambda_out, double* grad_force) {
+  if (c == nullptr || state_t == nullptr || state_t1 == nullptr || lambda_in == nullptr || lambda_out == nullptr ||
+      grad_force == nullptr || lambda_in == lambda_out)
+    return fail(LBF_EINVAL, "bad argument");
+  if (c->two) return fail(LBF_ENOTSUP, "the adjoint is single-component only");
+  if (c->adj.fn == nullptr) return fail(LBF_ENOTSUP, "the adjoint needs LBF_F32 or LBF_F64 storage");
+  AdjParams a;
+  std::memset(&a, 0, sizeof(a));
+  a.state_t = state_t;
+  a.state_t1 = state_t1;
+  a.lam_in = lambda_in;
+  a.lam_out = lambda_out;
+  a.grad_force = grad_force;
+  a.mask = c->mask_d;
+  a.force_field = c->prm.force_field;
+  for (int k = 0; k < 3; ++k) a.force[k] = c->prm.force[k];
+  a.omega = c->omega;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.N = c->N;
+  a.sc = c->sc;
+  a.zchunk = c->zchunk;
+  void* args[] = {&a};
+  LBF_CUDA(cudaLaunchKernel(c->adj.fn, c->fgrid, dim3(32, c->adj.by + 2, 1), args, c->adj.smem, c->stream));
+  return LBF_OK;
+}
+
+}  // extern "C"

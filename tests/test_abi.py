@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads and exports every symbol include/lbf.h declares; host-only
+entry points (validation, workspace layout, status strings) behave as documented. No GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2609_09160_gb300 import _lbf, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lbf.load_library()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lbf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbf_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_and_binding_agree():
+    assert declared_symbols() == sorted(_lbf.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def params(**kw):
+    p = _lbf.lbf_params()
+    p.lattice, p.nx, p.ny, p.nz, p.storage, p.tau = 19, 16, 16, 16, _lbf.LBF_F32, 0.8
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_workspace_holds_two_moment_buffers(lib):
+    """Two buffers of 10 fields: the paper's 20 scalar fields per site (Sec. 3 memory model)."""
+    for storage, b in ((_lbf.LBF_F64, 8), (_lbf.LBF_F32, 4), (_lbf.LBF_F16, 2), (_lbf.LBF_BF16, 2)):
+        p = params(nx=512, ny=512, nz=512, storage=storage)
+        need = _lbf.lbf_workspace_bytes(p)
+        moments = 20 * 512 ** 3 * b
+        assert moments <= need < moments + 64 * 2 ** 20
+    # FP64 512^3 moments = 20 GB exactly (GB = 2^30 bytes), as printed in Sec. 3
+    assert 20 * 512 ** 3 * 8 == 20 * 2 ** 30
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(lattice=15), _lbf.LBF_EINVAL),
+    (dict(nx=0), _lbf.LBF_EINVAL),
+    (dict(tau=0.5), _lbf.LBF_EINVAL),
+    (dict(storage=7), _lbf.LBF_EINVAL),
+    (dict(two_component=1, tau_l=1.0, tau_h=1.0, rho_l=0.5, rho_h=1.5, width=4.0, sigma=0.03, diffusivity=0.1),
+     _lbf.LBF_ENOTSUP),
+    (dict(two_component=1, tau_l=1.0, tau_h=0.4, rho_l=1.0, rho_h=1.0, width=4.0, sigma=0.03, diffusivity=0.1),
+     _lbf.LBF_EINVAL),
+])
+def test_validation_rejects_bad_parameters(lib, kw, status):
+    p = params(**kw)
+    assert _lbf.lbf_validate(p) == status
+    assert _lbf.lbf_workspace_bytes(p) == 0
+    assert _lbf.lbf_last_error()
+
+
+def test_valid_parameters(lib):
+    assert _lbf.lbf_validate(params()) == _lbf.LBF_OK
+    tc = params(two_component=1, tau_l=1.0, tau_h=0.8, rho_l=1.0, rho_h=1.0, width=4.0, sigma=0.03, diffusivity=0.1)
+    assert _lbf.lbf_validate(tc) == _lbf.LBF_OK
+
+
+def test_create_rejects_missing_or_small_workspace_before_touching_the_gpu(lib):
+    p = params()
+    with pytest.raises(_lbf.LBFError) as e:
+        _lbf.lbf_create(p, 0, 1 << 30)
+    assert e.value.status == _lbf.LBF_EINVAL
+    with pytest.raises(_lbf.LBFError) as e:
+        _lbf.lbf_create(p, 256, 1024)
+    assert e.value.status == _lbf.LBF_ENOMEM
+    with pytest.raises(_lbf.LBFError) as e:
+        _lbf.lbf_create(p, 4096 + 8, 1 << 40)
+    assert e.value.status == _lbf.LBF_ENOMEM
+
+
+def test_status_strings(lib):
+    names = [_lbf.lbf_status_string(s) for s in range(7)]
+    assert names == ["LBF_OK", "LBF_EINVAL", "LBF_ENOMEM", "LBF_ECUDA", "LBF_EUNSTABLE", "LBF_EINTERNAL",
+                     "LBF_ENOTSUP"]
+    assert _lbf.lbf_version() >= 1

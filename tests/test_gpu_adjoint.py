@@ -1,0 +1,123 @@
+"""GPU parity of the adjoint kernel and of the checkpointed Rollout with the oracle's FP64
+gradients, and the config-5 finite-difference check (128x64x64 channel, per-site force,
+500 steps, checkpoints every 50) in FP64 on the GPU."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import adjoint as oadj
+from paper_2609_09160_gb300 import Solver, rollout
+
+from _helpers import group_errors, rel_max
+
+pytestmark = pytest.mark.gpu
+LAT = {19: oracle.D3Q19, 27: oracle.D3Q27}
+CDT = {"f64": torch.float64, "f32": torch.float32}
+TOL_ADJ = {"f64": 1e-11, "f32": 2e-5}
+
+
+@pytest.mark.parametrize("lattice", [19, 27])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_adjoint_step_matches_oracle_vjp(lattice, storage):
+    shape = (7, 11, 33)
+    M = synth.random_moments(shape, seed=50, p_scale=1e-3, u_scale=0.03, neq_scale=1e-4)
+    mask = synth.channel_walls(shape) | synth.random_mask(shape, 0.08, seed=51)
+    F = synth.random_field(shape, 1e-4, seed=52, mask=mask)
+    lam_next = torch.from_numpy(np.random.default_rng(53).standard_normal((10,) + shape))
+    Fd = F.to(device="cuda", dtype=CDT[storage]).contiguous()
+    s = Solver(shape, lattice=lattice, tau=0.7, storage=storage, force=(2e-5, 0.0, 0.0), force_field=Fd, mask=mask)
+    s.set_moments(M.cuda())
+    M_t = s.moments().cpu()  # the state the GPU holds (storage rounding included)
+    st0, st1 = s.new_state(), s.new_state()
+    s.copy_state(st0)
+    s.copy_state(st1)  # solid sites of st1 are not written by the step
+    s.step_state(st0, st1)
+    lin = lam_next.to(device="cuda", dtype=CDT[storage]).contiguous()
+    lout = torch.empty_like(lin)
+    gF = torch.zeros((3,) + shape, dtype=torch.float64, device="cuda")
+    s.adjoint_step(st0, st1, lin, lout, gF)
+    Ftot = F.to(CDT[storage]).to(torch.float64) + torch.tensor([2e-5, 0.0, 0.0], dtype=torch.float64).reshape(3, 1, 1, 1)
+    lam_t, gF_ref = oadj.step_vjp(LAT[lattice], M_t, 0.7, Ftot, lam_next.to(CDT[storage]).to(torch.float64), mask)
+    err = group_errors(lout, lam_t)
+    assert max(err.values()) < TOL_ADJ[storage], err
+    assert rel_max(gF, gF_ref) < TOL_ADJ[storage]
+
+
+@pytest.mark.parametrize("lattice", [19, 27])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_rollout_gradient_matches_oracle(lattice, storage):
+    shape = (4, 10, 32)
+    steps, K, tau = 12, 5, 0.75
+    M0 = synth.random_moments(shape, seed=60, p_scale=1e-3, u_scale=0.02, neq_scale=1e-4)
+    mask = synth.channel_walls(shape)
+    F = synth.random_field(shape, 1e-4, seed=61, mask=mask)
+    u_tgt = synth.random_field(shape, 1e-3, seed=62)
+    Fd = F.to(device="cuda", dtype=CDT[storage]).contiguous().requires_grad_(True)
+    s = Solver(shape, lattice=lattice, tau=tau, storage=storage, force_field=Fd, mask=mask)
+    M0d = M0.to(device="cuda", dtype=CDT[storage]).requires_grad_(True)
+    MT = rollout(Fd, M0d, s, steps, K)
+    fluid = (~mask).to(device="cuda", dtype=MT.dtype)
+    d = (MT[1:4] - u_tgt.to(device="cuda", dtype=MT.dtype)) * fluid
+    L = (d * d).sum() / fluid.sum()
+    L.backward()
+    Lr, gM_ref, gF_ref = oadj.rollout_gradient(LAT[lattice], M0.to(CDT[storage]).double(), F.to(CDT[storage]).double(),
+                                               steps, tau, u_tgt, mask)
+    tol = 1e-10 if storage == "f64" else 1e-4
+    assert abs(L.item() - Lr.item()) < tol * Lr.item()
+    assert rel_max(s.grad_force64, gF_ref) < tol
+    errs = group_errors(M0d.grad, gM_ref)
+    assert max(errs.values()) < tol, errs
+
+
+def test_config5_adjoint_matches_central_differences():
+    """128(x) x 64(y) x 64(z) channel, walls at y = 0 and 63, per-site force N(0, 1e-12) on the
+    fluid, loss = mean |u(500) - u_target|^2 over the fluid, checkpoints every 50 steps. FP64 GPU
+    forward for the differences (eps = 1e-7 on one force component; eps 1e-6 gives the same
+    values: the loss is a near-quadratic function of F), 16 sites x 3 components, agreement 1e-4."""
+    shape = (64, 64, 128)
+    steps, K, tau = 500, 50, 0.9
+    mask = synth.channel_walls(shape)
+    F64 = synth.random_field(shape, 1e-6, seed=70, mask=mask).cuda().contiguous()
+    u_tgt = synth.random_field(shape, 1e-4, seed=71).cuda()
+    M0 = torch.zeros((10,) + shape, dtype=torch.float64, device="cuda")
+    fluid = (~mask).cuda().double()
+    nfl = fluid.sum()
+
+    Fd = F64.clone().requires_grad_(True)
+    s = Solver(shape, lattice=19, tau=tau, storage="f64", force_field=Fd, mask=mask)
+    MT = rollout(Fd, M0, s, steps, K)
+    d = (MT[1:4] - u_tgt) * fluid
+    L = (d * d).sum() / nfl
+    L.backward()
+    g = s.grad_force64
+
+    F_fd = F64.clone()
+    s_fd = Solver(shape, lattice=19, tau=tau, storage="f64", force_field=F_fd, mask=mask)
+
+    def loss():
+        s_fd.set_moments(M0)
+        s_fd.step(steps)
+        M = s_fd.moments()
+        dd = (M[1:4] - u_tgt) * fluid
+        return ((dd * dd).sum() / nfl).item()
+
+    rng = np.random.default_rng(72)
+    fl = torch.nonzero(~mask).numpy()
+    picks = fl[rng.choice(len(fl), 16, replace=False)]
+    gmax = g.abs().max().item()
+    for z, y, x in picks:
+        for a in range(3):
+            vals = []
+            for eps in (1e-7, 1e-6):
+                F_fd.copy_(F64)
+                F_fd[a, z, y, x] += eps
+                lp = loss()
+                F_fd[a, z, y, x] -= 2 * eps
+                lm = loss()
+                vals.append((lp - lm) / (2 * eps))
+            fd = vals[0]
+            assert abs(vals[0] - vals[1]) < 1e-4 * max(abs(fd), 1e-3 * gmax)  # plateau
+            got = g[a, z, y, x].item()
+            assert abs(got - fd) < 1e-4 * max(abs(fd), 1e-3 * gmax), (a, z, y, x, got, fd)
