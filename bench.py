@@ -140,6 +140,31 @@ def gpu_identifier(torch, dev):
         return str(dev)
 
 
+WORKLOADS = {
+    # key: (lattice, storage, builder) -- the headline is "channel256"
+    "channel256": (19, "f32", "channel"),
+    "tg512_d3q27_f32": (27, "f32", "tg512"),
+    "tg512_d3q27_f16": (27, "f16", "tg512"),
+    "tg512_d3q27_bf16": (27, "bf16", "tg512"),
+    "tg512_d3q19_f32": (19, "f32", "tg512"),
+    "tg512_d3q19_f16": (19, "f16", "tg512"),
+}
+
+
+def workload_solver(torch, device, key):
+    """Solver + initial state of a named workload (returns solver, public state, mask)."""
+    lattice, storage, kind = WORKLOADS[key]
+    if kind == "channel":
+        return channel_solver(torch, device, storage, lattice)
+    import synth
+    from paper_2609_09160_gb300 import Solver
+
+    n = 512
+    M0 = synth.taylor_green_perturbed(n, 0.04, 0.55, 0.01, seed=3, dtype=torch.float32, device=device)
+    s = Solver((n, n, n), lattice=lattice, tau=0.55, storage=storage, device=device)
+    return s, M0, None
+
+
 def channel_solver(torch, device, storage="f32", lattice=19, shape=SHAPE):
     import synth
     from paper_2609_09160_gb300 import Solver
@@ -307,8 +332,9 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         barrier = dist.barrier
-    s, M0, solid = channel_solver(torch, device)
+    s, M0, solid = workload_solver(torch, device, args.workload)
     s.set_moments(M0.to(device))
+    del M0
     with ClockSampler(gpu_identifier(torch, device)) as clk:
         t = time_steps(torch, s, args.steps, args.warmup, barrier)
     clocks = clk.summary()
@@ -324,26 +350,31 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     peak, peak_kind = measured_peaks()
-    bpl = algorithmic_bytes("f32", mask=True)
+    lattice, storage, kind = WORKLOADS[args.workload]
+    bpl = algorithmic_bytes(storage, mask=(kind == "channel"))
     t_launch = t / args.steps
     achieved = bpl * n / t_launch / 1e9
-    traffic = ncu_traffic("channel256_d3q19_f32")
+    traffic = ncu_traffic(args.workload)
+    desc = WORKLOAD if args.workload == "channel256" else (
+        f"D3Q{lattice} {storage.upper()} storage, 512^3 periodic Taylor-Green U0=0.04 + random-phase perturbation "
+        "RMS 0.01 (seed 3), tau=0.55")
+    shape_xyz = [256, 256, 256] if kind == "channel" else [512, 512, 512]
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "D3Q19", "shape_xyz": [256, 256, 256], "storage": "f32",
-                   "l2": "inputs larger than L2 (2 x 671 MB moment buffers), no flush",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if storage == "f64" else "f32", "data": "synthetic",
+        "config": {"workload": desc, "lattice": f"D3Q{lattice}", "shape_xyz": shape_xyz, "storage": storage,
+                   "l2": "inputs larger than L2 (two moment buffers of >= 671 MB), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "k_stream_collide<D3Q19,float,8,mask>", "bytes_per_lup": bpl,
-                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+                     "kernel": f"k_stream_collide<D3Q{lattice},{storage},{'mask' if kind == 'channel' else 'periodic'}>",
+                     "bytes_per_lup": bpl, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "sums_after": {"sum_p": sums[0], "sum_ux": sums[1]},
     }
-    if world == 1:
+    if world == 1 and not args.kernel_only and args.workload == "channel256":
         line["e2e"] = e2e_measure(torch, device, args.steps)
         line["cpu_baseline"] = cpu_baseline_oracle()
         if not args.quick:
@@ -402,7 +433,10 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--quick", action="store_true", help="headline only: skip the secondary rows")
+    ap.add_argument("--quick", action="store_true", help="skip the secondary rows")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only the device-timed steps (no e2e, CPU baseline or secondary rows): for profiling")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="channel256")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -35,8 +35,13 @@ def _inputs():
     return files
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def up_to_date(tuning=()):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+        return False
+    if open(STAMP).read() != " ".join(tuning):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _inputs())
@@ -55,11 +60,13 @@ def _compile(src, extra):
 
 
 def build(force=False, verbose_ptxas=False):
-    """Compile liblbf.so in place; returns its path."""
-    if not force and up_to_date():
+    """Compile liblbf.so in place; returns its path. LBF_NVCC_EXTRA (space-separated nvcc flags,
+    e.g. tile-size defines) is appended for tuning builds and forces a rebuild."""
+    tuning = os.environ.get("LBF_NVCC_EXTRA", "").split()
+    if not force and up_to_date(tuning):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + tuning
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
@@ -69,6 +76,8 @@ def build(force=False, verbose_ptxas=False):
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr[-4000:]}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(tuning))
     return LIB
 
 

@@ -1,5 +1,7 @@
 // Host side of the C ABI declared in include/lbf.h: parameter validation, workspace layout,
 // context state, stream-ordered launches and host <-> device staging.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,7 +36,12 @@ lbf_status fail(lbf_status s, const std::string& msg) {
 
 constexpr size_t kAlign = 256;
 constexpr size_t kStagingMax = size_t(16) << 20;
-constexpr double kTarget16 = 4096.0;  // 16-bit: the largest magnitude of a group maps near 2^12
+// 16-bit storage: each group g is multiplied by 2^s_g so that the larger of 16x its initial
+// maximum and a physical bound (|p*| = |rho - 1| <= 0.1, |u| <= 0.4 (the stability guard),
+// |a2 - u u| <= 0.05) maps to at most 2^15 (FP16 overflows above 65504). Within that range FP16
+// keeps its 11-bit significand down to 2^-14 / 2^s, so the floors cost no precision.
+constexpr double kTarget16 = 32768.0;
+constexpr double kFloor16[3] = {0.1, 0.4, 0.05};
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -82,7 +89,8 @@ lbf_status check_params(const lbf_params* p) {
 }
 
 int grid_x(int nx) { return (nx + FwdTile<8>::XOUT - 1) / FwdTile<8>::XOUT; }
-int grid_y(int ny, int storage) { const int by = tile_rows(storage); return (ny + by - 1) / by; }
+int grid_y(int ny, int by) { return (ny + by - 1) / by; }
+int fwd_by(int storage) { return fwd_rows(storage == LBF_F64); }
 int min_zchunk(int nz) { return std::min(8, nz); }
 
 bool make_layout(const lbf_params* p, Layout* L) {
@@ -108,7 +116,7 @@ bool make_layout(const lbf_params* p, Layout* L) {
     L->phi[0] = L->phi[1] = L->F[0] = L->F[1] = L->G = 0;
   }
   const long long gz = (p->nz + min_zchunk(p->nz) - 1) / min_zchunk(p->nz);
-  L->npartials = std::max<long long>((long long)grid_x(p->nx) * grid_y(p->ny, p->storage) * gz, 1024);
+  L->npartials = std::max<long long>((long long)grid_x(p->nx) * grid_y(p->ny, fwd_by(p->storage)) * gz, 1024);
   L->partials = take(size_t(L->npartials) * 8 * sizeof(double));
   L->scal = take(64 * sizeof(double));
   L->staging_bytes = std::min<size_t>(kStagingMax, size_t(11) * 8 * size_t(N));
@@ -119,8 +127,10 @@ bool make_layout(const lbf_params* p, Layout* L) {
 
 float pow2f(int s) { return std::ldexp(1.0f, s); }
 
-int choose_shift(double maxabs, double fallback) {
-  const double m = maxabs > 0.0 && std::isfinite(maxabs) ? maxabs : fallback;
+int choose_shift(double maxabs, int group, bool hinted) {
+  double m = maxabs > 0.0 && std::isfinite(maxabs) ? maxabs : 0.0;
+  if (!hinted) m = std::max(16.0 * m, kFloor16[group]);
+  if (!(m > 0.0)) m = kFloor16[group];
   int s = (int)std::floor(std::log2(kTarget16 / m));
   return std::max(-30, std::min(60, s));
 }
@@ -151,8 +161,10 @@ struct lbf_ctx {
   Scales sc;
   cudaStream_t stream;
   int zchunk;
-  dim3 fgrid;
+  dim3 fgrid, agrid;
   KernelInfo fwd, adj;
+  bool tma;             // the forward kernel stages plane patches with TMA
+  CUtensorMap tmap[2];  // tensor maps of the two state buffers (TMA source)
   bool sums_valid;
   bool unstable_seen;
   double omega, nu_l, nu_h;
@@ -160,9 +172,35 @@ struct lbf_ctx {
 
 namespace {
 
-KernelInfo forward_for(int Q, int storage, bool mask, bool two) {
-  return Q == 19 ? forward_kernel_q19(storage, mask, two) : forward_kernel_q27(storage, mask, two);
+KernelInfo forward_for(int Q, int storage, bool mask, bool two, bool tma) {
+  return Q == 19 ? forward_kernel_q19(storage, mask, two, tma) : forward_kernel_q27(storage, mask, two, tma);
 }
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// TMA is used when a row of the state is a whole number of 16-byte units (the tensor map needs
+// 16-byte strides) and the driver provides the encoder
+bool tma_eligible(int storage, int nx) {
+  return (size_t(nx) * storage_bytes(storage)) % 16 == 0 && tensor_map_encoder() != nullptr &&
+         std::getenv("LBF_NO_TMA") == nullptr;
+}
+
+// 4-D map over a state buffer: dims (x, y, z, field), box (box_x, rows, 1, 10)
+lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out);
 KernelInfo adjoint_for(int Q, int storage, bool mask) {
   return Q == 19 ? adjoint_kernel_q19(storage, mask) : adjoint_kernel_q27(storage, mask);
 }
@@ -170,6 +208,8 @@ KernelInfo adjoint_for(int Q, int storage, bool mask) {
 lbf_status prepare(const KernelInfo& k) {
   if (k.fn == nullptr) return LBF_OK;
   LBF_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+  // all of the unified L1/shared storage as shared memory: the rings decide how many CTAs fit
+  LBF_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   return LBF_OK;
 }
 
@@ -319,9 +359,41 @@ FwdParams forward_params(const lbf_ctx* c, const void* src, void* dst, bool redu
   return a;
 }
 
+lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out) {
+  CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  switch (c->storage) {
+    case LBF_F64: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
+    case LBF_F32: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+    case LBF_F16: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+    case LBF_BF16: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+  }
+  const cuuint64_t es = storage_bytes(c->storage);
+  const cuuint64_t dims[4] = {cuuint64_t(c->nx), cuuint64_t(c->ny), cuuint64_t(c->nz), 10};
+  const cuuint64_t strides[3] = {es * c->nx, es * c->nx * c->ny, es * cuuint64_t(c->N)};
+  const cuuint32_t box[4] = {cuuint32_t(c->fwd.box_x), cuuint32_t(c->fwd.by + 2), 1, 10};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = tensor_map_encoder()(out, dt, 4, const_cast<void*>(base), dims, strides, box, estr,
+                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(LBF_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string(int(r)));
+  return LBF_OK;
+}
+
 lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
   FwdParams a = forward_params(c, src, dst, reduce);
-  void* args[] = {&a};
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  if (c->tma) {
+    if (src == c->state[0]) {
+      tm = c->tmap[0];
+    } else if (src == c->state[1]) {
+      tm = c->tmap[1];
+    } else {
+      lbf_status st = encode_state_map(c, src, &tm);
+      if (st != LBF_OK) return st;
+    }
+  }
+  void* args[] = {&a, &tm};
   LBF_CUDA(cudaLaunchKernel(c->fwd.fn, c->fgrid, dim3(32, c->fwd.by + 2, 1), args, c->fwd.smem, c->stream));
   return LBF_OK;
 }
@@ -355,11 +427,10 @@ lbf_status reduce_state(lbf_ctx* c) {
 }
 
 void set_scales(lbf_ctx* c, const double m[3]) {
-  const double fallback[3] = {1e-3, 0.1, 1e-3};
   for (int g = 0; g < 3; ++g) {
     if (c->storage == LBF_F16 || c->storage == LBF_BF16) {
       const double hint = c->prm.scale_hint[g];
-      const int s = choose_shift(hint > 0.0 ? hint : m[g], fallback[g]);
+      const int s = hint > 0.0 ? choose_shift(hint, g, true) : choose_shift(m[g], g, false);
       c->sc.enc[g] = pow2f(s);
       c->sc.dec[g] = pow2f(-s);
     } else {
@@ -460,7 +531,8 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   const double m0[3] = {0.0, 0.0, 0.0};
   set_scales(c, m0);
 
-  c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two);
+  c->tma = tma_eligible(c->storage, c->nx);
+  c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two, c->tma);
   c->adj = adjoint_for(c->Q, c->storage, c->has_mask);
   if (c->fwd.fn == nullptr) {
     delete c;
@@ -473,23 +545,42 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   if ((st = prepare(c->fwd)) != LBF_OK) return cleanup(st);
   if ((st = prepare(c->adj)) != LBF_OK) return cleanup(st);
 
-  // z-chunk: enough CTAs for about two waves of resident blocks, at least 8 planes per chunk
+  // z-chunk: the CTAs of one (x, y) tile column march through nz / chunks planes each. Choose the
+  // chunk count that minimises (1 + restaged planes) / (fraction of the last wave that is busy).
   int dev = 0, sms = 1, per_sm = 1;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c->fwd.fn, c->fwd.threads, c->fwd.smem) != cudaSuccess)
     return cleanup(fail(LBF_ECUDA, std::string("device query failed: ") + cudaGetErrorString(cudaGetLastError())));
   per_sm = std::max(per_sm, 1);
-  const long long tiles = (long long)grid_x(c->nx) * grid_y(c->ny, c->storage);
-  const long long want = 2LL * sms * per_sm;
-  long long chunks = std::max<long long>(1, (want + tiles - 1) / tiles);
-  int zc = (int)std::max<long long>(min_zchunk(c->nz), (c->nz + chunks - 1) / chunks);
+  const long long tiles = (long long)grid_x(c->nx) * grid_y(c->ny, c->fwd.by);
+  const double resident = double(sms) * per_sm;
+  int zc = c->nz;
+  double best = 1e30;
+  for (int chunks = 1; chunks <= c->nz; ++chunks) {
+    const int z = (c->nz + chunks - 1) / chunks;
+    if (z < min_zchunk(c->nz)) break;
+    if (z > 64) continue;  // long chunks leave too few CTAs to overlap their pipelines
+    const long long nchunks = (c->nz + z - 1) / z;
+    const double waves = double(tiles * nchunks) / resident;
+    const double busy = waves / std::ceil(waves);
+    const double cost = (1.0 + 2.0 / z) / busy;
+    if (cost < best - 1e-9) {
+      best = cost;
+      zc = z;
+    }
+  }
   if (const char* e = std::getenv("LBF_ZCHUNK")) {
     const int v = std::atoi(e);
     if (v >= 1) zc = std::max(min_zchunk(c->nz), v);
   }
   c->zchunk = std::min(zc, c->nz);
-  c->fgrid = dim3(grid_x(c->nx), grid_y(c->ny, c->storage), (c->nz + c->zchunk - 1) / c->zchunk);
+  c->fgrid = dim3(grid_x(c->nx), grid_y(c->ny, c->fwd.by), (c->nz + c->zchunk - 1) / c->zchunk);
+  c->agrid = c->adj.fn ? dim3(grid_x(c->nx), grid_y(c->ny, c->adj.by), (c->nz + c->zchunk - 1) / c->zchunk) : dim3(1, 1, 1);
+  if (c->tma) {
+    for (int k = 0; k < 2; ++k)
+      if ((st = encode_state_map(c, c->state[k], &c->tmap[k])) != LBF_OK) return cleanup(st);
+  }
   if (forward_blocks(c) > L.npartials) return cleanup(fail(LBF_EINTERNAL, "partials buffer too small"));
 
   cudaStream_t s = c->stream;
@@ -671,6 +762,8 @@ lbf_status lbf_synchronize(lbf_ctx* c) {
   unsigned f = 0;
   LBF_CUDA(cudaMemcpyAsync(&f, c->flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
   LBF_CUDA(cudaStreamSynchronize(c->stream));
+  if (f & 6u) return fail(LBF_EINTERNAL, (f & 4u) ? "a TMA stage was misaligned; the step was abandoned"
+                                                  : "a TMA plane load did not complete in time; the step was abandoned");
   if (f & 1u) c->unstable_seen = true;
   return c->unstable_seen ? fail(LBF_EUNSTABLE, "non-finite value or |u| > 0.4 in a step") : LBF_OK;
 }
@@ -727,7 +820,7 @@ lbf_status lbf_adjoint_step(lbf_ctx* c, const void* state_t, const void* state_t
   a.sc = c->sc;
   a.zchunk = c->zchunk;
   void* args[] = {&a};
-  LBF_CUDA(cudaLaunchKernel(c->adj.fn, c->fgrid, dim3(32, c->adj.by + 2, 1), args, c->adj.smem, c->stream));
+  LBF_CUDA(cudaLaunchKernel(c->adj.fn, c->agrid, dim3(32, c->adj.by + 2, 1), args, c->adj.smem, c->stream));
   return LBF_OK;
 }
 

@@ -22,6 +22,7 @@
 #pragma once
 
 #include "lattice.cuh"
+#include "tma.cuh"
 
 namespace lbf {
 
@@ -165,25 +166,120 @@ struct FwdTile {
   static constexpr int XOUT = 30;
 };
 
+// shared memory of a ring that keeps all Q populations of 3 planes (used by the adjoint kernel)
 template <class L, class T, int BY, bool MASK>
-constexpr size_t fwd_smem_bytes() {
+constexpr size_t ring3_smem_bytes() {
   return size_t(3) * L::Q * FwdTile<BY>::ROWS * 32 * sizeof(T) + (MASK ? size_t(3) * FwdTile<BY>::ROWS * 32 : 0);
 }
 
-template <class L, class S, int BY, bool MASK, bool TWO>
-__global__ void __launch_bounds__(FwdTile<BY>::THREADS)
-    k_stream_collide(const FwdParams a) {
+// ---------------------------------------------------------------------------------------------
+// Population ring of the forward kernel, split by c_z. A population of plane p travelling along c
+// is read by the output plane p + c_z, and (bounce-back) by its own site at plane p. With the two
+// barriers of an iteration (after staging plane z+1, after the outputs of plane z) a group needs
+//   c_z = -1: 2 plane slots, c_z = 0: 2 slots, c_z = +1: 3 slots.
+// The three axial directions (rest, (0,0,+1), (0,0,-1)) only move along the thread's own column
+// and live in registers, so the ring holds Q - 3 directions.
+template <class L>
+struct Dirs {
+  __host__ __device__ static constexpr bool axial(int q) { return L::cx(q) == 0 && L::cy(q) == 0; }
+  __host__ __device__ static constexpr int group(int q) { return L::cz(q) + 1; }
+  __host__ __device__ static constexpr int gidx(int q) {
+    int n = 0;
+    for (int k = 0; k < q; ++k)
+      if (!axial(k) && group(k) == group(q)) ++n;
+    return n;
+  }
+  __host__ __device__ static constexpr int gsize(int g) {
+    int n = 0;
+    for (int k = 0; k < L::Q; ++k)
+      if (!axial(k) && group(k) == g) ++n;
+    return n;
+  }
+  __host__ __device__ static constexpr int find(int cx, int cy, int cz) {
+    for (int k = 0; k < L::Q; ++k)
+      if (L::cx(k) == cx && L::cy(k) == cy && L::cz(k) == cz) return k;
+    return -1;
+  }
+};
+
+template <class L, int ROWS>
+struct GroupRing {
+  using D = Dirs<L>;
+  static constexpr int SITES = ROWS * 32;
+  static constexpr int NS0 = 2, NS1 = 2, NS2 = 3;
+  __host__ __device__ static constexpr int base(int g) {
+    return g == 0 ? 0 : (g == 1 ? NS0 * D::gsize(0) * SITES : (NS0 * D::gsize(0) + NS1 * D::gsize(1)) * SITES);
+  }
+  static constexpr int VALUES = (NS0 * D::gsize(0) + NS1 * D::gsize(1) + NS2 * D::gsize(2)) * SITES;
+};
+
+// TMA box of one plane patch: all 10 fields x ROWS rows x BX columns. The first column is the
+// lane-0 site rounded down to a 16-byte boundary (A elements), so BX covers 32 lanes + A - 1.
+template <class S>
+struct TmaBox {
+  static constexpr int A = 16 / int(sizeof(S));
+  static constexpr int BX = ((32 + A - 1) + A - 1) / A * A;
+};
+constexpr int kRawStages = 2;  // plane patches in flight per CTA
+
+// a TMA destination in shared memory must start on a 128-byte boundary: every stage of the raw
+// ring is padded to a multiple of 128 bytes and the ring itself is aligned inside the dynamic
+// shared memory (128 bytes of slack)
+template <class S, int ROWS>
+constexpr size_t raw_stage_bytes() {
+  return (size_t(10) * ROWS * TmaBox<S>::BX * sizeof(S) + 127) / 128 * 128;
+}
+
+template <class L, class S, int BY, bool MASK, bool TMA>
+constexpr size_t fwd_smem_bytes() {
   using T = typename ComputeOf<S>::type;
+  const size_t raw = TMA ? 128 + size_t(kRawStages) * raw_stage_bytes<S, BY + 2>() : 0;
+  return raw + size_t(GroupRing<L, BY + 2>::VALUES) * sizeof(T) + (MASK ? size_t(3) * (BY + 2) * 32 : 0);
+}
+
+// per-site inputs other than the 10 stored fields, prefetched one plane ahead
+template <class T, bool TWO>
+struct SiteExtra {
+  T F[3];     // force at the site: uniform (+ field), or F^n for two components
+  T phi_o;    // two components: phi^n (source side)
+  T Fn[3];    // two components: F^{n+1} (correction side)
+  T phi_n;    // two components: phi^{n+1}
+  bool solid;
+};
+
+// minimum resident CTAs per SM asked of the register allocator (320-thread CTAs: 3 -> <= 64
+// registers per thread)
+#ifndef LBF_FWD_MINB
+#define LBF_FWD_MINB 3
+#endif
+
+constexpr uint32_t kWaitPolls = 1u << 20;  // bound of every mbarrier wait
+
+template <class L, class S, int BY, bool MASK, bool TWO, bool TMA>
+__global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>::value ? 1 : LBF_FWD_MINB)
+    k_stream_collide(const FwdParams a, const __grid_constant__ CUtensorMap tmap) {
+  using T = typename ComputeOf<S>::type;
+  using D = Dirs<L>;
+  using R = GroupRing<L, BY + 2>;
   constexpr int Q = L::Q;
-  constexpr int ROWS = FwdTile<BY>::ROWS;
-  constexpr int REST = rest_index<L>();
-  constexpr int PLANE = Q * ROWS * 32;  // populations of one ring slot
-  static_assert(fwd_smem_bytes<L, T, BY, MASK>() >= 6 * 512 * sizeof(double), "ring too small for the final tree");
+  constexpr int ROWS = BY + 2;
+  constexpr int SITES = ROWS * 32;
+  constexpr int QREST = D::find(0, 0, 0);
+  constexpr int QUP = D::find(0, 0, 1);
+  constexpr int QDN = D::find(0, 0, -1);
+  constexpr int BX = TmaBox<S>::BX, AL = TmaBox<S>::A;
+  constexpr int STAGE_ELEMS = 10 * ROWS * BX;                                  // one box
+  constexpr int STAGE_STRIDE = int(raw_stage_bytes<S, ROWS>() / sizeof(S));   // padded stage
+  constexpr size_t RAW_BYTES = TMA ? 128 + size_t(kRawStages) * raw_stage_bytes<S, ROWS>() : 0;
+  static_assert(fwd_smem_bytes<L, S, BY, MASK, TMA>() >= 6 * 512 * sizeof(double), "smem too small for the final tree");
   static_assert(FwdTile<BY>::THREADS <= 512, "final tree assumes <= 512 threads");
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* pop = reinterpret_cast<T*>(smem_raw);
-  uint8_t* msk = reinterpret_cast<uint8_t*>(smem_raw + size_t(3) * PLANE * sizeof(T));
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  S* rawst = reinterpret_cast<S*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+  T* ring = reinterpret_cast<T*>(smem_raw + RAW_BYTES);
+  uint8_t* msk = reinterpret_cast<uint8_t*>(smem_raw + RAW_BYTES + size_t(R::VALUES) * sizeof(T));
+  __shared__ __align__(8) uint64_t bars[kRawStages];
+  __shared__ int abort_flag;
   __shared__ double red_s[ROWS][6];
 
   const S* __restrict__ src = static_cast<const S*>(a.src);
@@ -191,206 +287,369 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS)
   const T* __restrict__ ffield = static_cast<const T*>(a.force_field);
 
   const int lane = threadIdx.x, row = threadIdx.y;
-  const int gx = blockIdx.x * FwdTile<BY>::XOUT - 1 + lane;
+  const int x0 = blockIdx.x * FwdTile<BY>::XOUT;
+  const int gx = x0 - 1 + lane;
   const int gy = blockIdx.y * BY - 1 + row;
   const int sx = ((gx % a.nx) + a.nx) % a.nx;
   const int sy = ((gy % a.ny) + a.ny) % a.ny;
   const bool outcol = lane >= 1 && lane <= FwdTile<BY>::XOUT && row >= 1 && row <= BY && gx < a.nx && gy < a.ny;
+  const bool inbox = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;  // TMA delivers this site
+  const bool needed = gx <= a.nx && gy <= a.ny;                      // read by some output
+  const int xa = ((x0 - 1 + AL) / AL - 1) * AL;                      // floor to AL; x0 - 1 >= -1
+  const int xoff = x0 - 1 - xa;
   const long long plane = (long long)a.nx * a.ny;
-  const long long col = (long long)sy * a.nx + sx;
+  const int col = sy * a.nx + sx;
   const long long N = a.N;
   const int z0 = blockIdx.z * a.zchunk;
   const int z1 = min(a.nz, z0 + a.zchunk);
   const int me = row * 32 + lane;
-
   const T one_m_omega = T(1) - T(a.omega);
-  const T Fu[3] = {T(a.force[0]), T(a.force[1]), T(a.force[2])};
+  const T Fu0 = T(a.force[0]), Fu1 = T(a.force[1]), Fu2 = T(a.force[2]);
+  const bool has_field = ffield != nullptr;
+  const int pbase = z0 - 1;  // first plane of this chunk's window (planes z0-1 .. z1 are staged)
 
-  // own-site values needed by the output of the plane staged one iteration earlier
-  T Fown[3] = {Fu[0], Fu[1], Fu[2]};
-  T Fnext[3] = {Fu[0], Fu[1], Fu[2]};
-  T inv2rho_own = T(0.5), inv2rho_next = T(0.5);
-  T phi_own = T(0), phi_next = T(0);
-  bool solid_own = false, solid_next = false;
+  // -- TMA issue / wait (plane p lives in stage (p - pbase) % kRawStages) ---------------------
+  auto issue = [&](int p) {  // elected thread only
+    if (p > z1 || abort_flag) return;
+    const int s = (p - pbase) % kRawStages;
+    S* dstp = rawst + s * STAGE_STRIDE;
+    if ((smem_u32(dstp) & 127u) != 0u) {  // never issue a copy the hardware would reject
+      atomicOr(a.flags, 4u);
+      abort_flag = 1;
+      return;
+    }
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bars[s], uint32_t(STAGE_ELEMS * sizeof(S)));
+    tma_load_4d(dstp, &tmap, &bars[s], xa, int(blockIdx.y) * BY - 1, wrap(p, a.nz), 0);
+  };
+  auto wait_plane = [&](int p) {
+    if (abort_flag) return;
+    const int s = (p - pbase) % kRawStages;
+    const uint32_t parity = uint32_t((p - pbase) / kRawStages) & 1u;
+    if (!mbar_wait_bounded(&bars[s], parity, kWaitPolls)) {
+      atomicOr(a.flags, 2u);
+      abort_flag = 1;
+    }
+  };
 
-  auto stage = [&](int zp, int slot) -> bool {
-    const int z = wrap(zp, a.nz);
-    const long long site = (long long)z * plane + col;
-    const T p = ld_field<S, T>(src, site, a.sc.dec[0]);
-    const T ux = ld_field<S, T>(src, N + site, a.sc.dec[1]);
-    const T uy = ld_field<S, T>(src, 2 * N + site, a.sc.dec[1]);
-    const T uz = ld_field<S, T>(src, 3 * N + site, a.sc.dec[1]);
-    const T nxx = ld_field<S, T>(src, 4 * N + site, a.sc.dec[2]);
-    const T nyy = ld_field<S, T>(src, 5 * N + site, a.sc.dec[2]);
-    const T nzz = ld_field<S, T>(src, 6 * N + site, a.sc.dec[2]);
-    const T nxy = ld_field<S, T>(src, 7 * N + site, a.sc.dec[2]);
-    const T nxz = ld_field<S, T>(src, 8 * N + site, a.sc.dec[2]);
-    const T nyz = ld_field<S, T>(src, 9 * N + site, a.sc.dec[2]);
-    T F[3] = {Fu[0], Fu[1], Fu[2]};
-    T inv2rho = T(0.5);
-    T omm = one_m_omega;
+  // -- per-site extras (mask, force, phase field), register prefetch ---------------------------
+  auto load_extra = [&](int zp, SiteExtra<T, TWO>& e) {
+    const long long zoff = (long long)wrap(zp, a.nz) * plane;
     if constexpr (TWO) {
-      const T* phi_o = static_cast<const T*>(a.phi_old);
-      const T* F_o = static_cast<const T*>(a.F_old);
-      const T ph = __ldg(phi_o + site);
-      const T rho = T(a.rho_l) + ph * T(a.rho_h - a.rho_l);
-      const T nu = T(a.nu_l) + ph * T(a.nu_h - a.nu_l);
-      inv2rho = T(0.5) / rho;
-      omm = T(1) - T(1) / (T(3) * nu + T(0.5));
-      F[0] = __ldg(F_o + site);
-      F[1] = __ldg(F_o + N + site);
-      F[2] = __ldg(F_o + 2 * N + site);
+      const T* po = static_cast<const T*>(a.phi_old) + zoff;
+      const T* Fo = static_cast<const T*>(a.F_old) + zoff;
+      e.phi_o = __ldg(po + col);
+      e.F[0] = __ldg(Fo + col);
+      e.F[1] = __ldg(Fo + N + col);
+      e.F[2] = __ldg(Fo + 2 * N + col);
       if (outcol) {
-        const T* phi_n = static_cast<const T*>(a.phi_new);
-        const T* F_n = static_cast<const T*>(a.F_new);
-        phi_next = __ldg(phi_n + site);
-        inv2rho_next = T(0.5) / (T(a.rho_l) + phi_next * T(a.rho_h - a.rho_l));
-        Fnext[0] = __ldg(F_n + site);
-        Fnext[1] = __ldg(F_n + N + site);
-        Fnext[2] = __ldg(F_n + 2 * N + site);
+        const T* pn = static_cast<const T*>(a.phi_new) + zoff;
+        const T* Fn = static_cast<const T*>(a.F_new) + zoff;
+        e.phi_n = __ldg(pn + col);
+        e.Fn[0] = __ldg(Fn + col);
+        e.Fn[1] = __ldg(Fn + N + col);
+        e.Fn[2] = __ldg(Fn + 2 * N + col);
       }
     } else {
-      if (ffield != nullptr) {
-        F[0] += __ldg(ffield + site);
-        F[1] += __ldg(ffield + N + site);
-        F[2] += __ldg(ffield + 2 * N + site);
+      e.F[0] = Fu0;
+      e.F[1] = Fu1;
+      e.F[2] = Fu2;
+      if (has_field) {
+        const T* fb = ffield + zoff;
+        e.F[0] += __ldg(fb + col);
+        e.F[1] += __ldg(fb + N + col);
+        e.F[2] += __ldg(fb + 2 * N + col);
       }
-      Fnext[0] = F[0];
-      Fnext[1] = F[1];
-      Fnext[2] = F[2];
     }
-    const PostColl<T> P = post_collision<T>(p, ux, uy, uz, nxx, nyy, nzz, nxy, nxz, nyz, F[0], F[1], F[2],
-                                            inv2rho, omm);
-    T* ps = pop + slot * PLANE + me;
+    if constexpr (MASK) e.solid = __ldg(a.mask + zoff + col) != 0;
+    else e.solid = false;
+  };
+
+  // the 10 stored values of this thread's site in plane p
+  auto read_raw = [&](int p, T (&m)[10]) {
+    if (TMA && inbox) {
+      const S* b = rawst + ((p - pbase) % kRawStages) * STAGE_STRIDE + row * BX + lane + xoff;
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        const float dec = k == 0 ? a.sc.dec[0] : (k < 4 ? a.sc.dec[1] : a.sc.dec[2]);
+        if constexpr (Codec<S>::scaled)
+          m[k] = static_cast<T>(static_cast<float>(b[k * ROWS * BX]) * dec);
+        else
+          m[k] = static_cast<T>(b[k * ROWS * BX]);
+      }
+    } else if (needed || !TMA) {
+      const S* __restrict__ bz = src + (long long)wrap(p, a.nz) * plane;
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        const float dec = k == 0 ? a.sc.dec[0] : (k < 4 ? a.sc.dec[1] : a.sc.dec[2]);
+        m[k] = ld_field<S, T>(bz + k * N, col, dec);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 10; ++k) m[k] = T(0);
+    }
+  };
+
+  // own-site values of the planes being output (carried from staging)
+  T Fown[3] = {Fu0, Fu1, Fu2}, Fnext[3] = {Fu0, Fu1, Fu2};
+  T i2r_own = T(0.5), i2r_next = T(0.5);
+  T phi_own = T(0), phi_next = T(0);
+  // axial populations of the own column: up(z-1), up(z), dn(z), rest(z) and the new plane's
+  T up_m1 = T(0), up_0 = T(0), dn_0 = T(0), rest_0 = T(0);
+  T up_new = T(0), dn_new = T(0), rest_new = T(0);
+  bool sol_m1 = false, sol_0 = false, sol_new = false;
+
+  // -- staging: post-collision populations of plane p into the ring ----------------------------
+  auto stage = [&](int p, const SiteExtra<T, TWO>& e) -> bool {
+    T m[10];
+    read_raw(p, m);
+    T inv2rho = T(0.5), omm = one_m_omega;
+    if constexpr (TWO) {
+      const T rho = T(a.rho_l) + e.phi_o * T(a.rho_h - a.rho_l);
+      const T nu = T(a.nu_l) + e.phi_o * T(a.nu_h - a.nu_l);
+      inv2rho = T(0.5) / rho;
+      omm = T(1) - T(1) / (T(3) * nu + T(0.5));
+      if (outcol) {
+        phi_next = e.phi_n;
+        i2r_next = T(0.5) / (T(a.rho_l) + e.phi_n * T(a.rho_h - a.rho_l));
+        Fnext[0] = e.Fn[0];
+        Fnext[1] = e.Fn[1];
+        Fnext[2] = e.Fn[2];
+      }
+    } else {
+      Fnext[0] = e.F[0];
+      Fnext[1] = e.F[1];
+      Fnext[2] = e.F[2];
+    }
+    const PostColl<T> P = post_collision<T>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9], e.F[0],
+                                            e.F[1], e.F[2], inv2rho, omm);
+    const int par = (p + 6) & 1, m3 = (p + 6) % 3;
+    T* g0 = ring + R::base(0) + par * D::gsize(0) * SITES + me;
+    T* g1 = ring + R::base(1) + par * D::gsize(1) * SITES + me;
+    T* g2 = ring + R::base(2) + m3 * D::gsize(2) * SITES + me;
+    auto put = [&](auto qc, T v) {
+      constexpr int q = decltype(qc)::value;
+      if constexpr (q == QUP) {
+        up_new = v;
+      } else if constexpr (q == QDN) {
+        dn_new = v;
+      } else {
+        constexpr int g = D::group(q);
+        T* b = g == 0 ? g0 : (g == 1 ? g1 : g2);
+        b[D::gidx(q) * SITES] = v;
+      }
+    };
     static_for<Q>([&](auto qc) {
       constexpr int q = decltype(qc)::value;
-      if constexpr (q == REST) {
-        ps[q * ROWS * 32] = T(L::w(q)) * P.q0;
+      if constexpr (q == QREST) {
+        rest_new = T(L::w(q)) * P.q0;
       } else if constexpr (q < L::opp(q)) {
         T fq, fo;
         pop_pair<L, q, T>(P, fq, fo);
-        ps[q * ROWS * 32] = fq;
-        ps[L::opp(q) * ROWS * 32] = fo;
+        put(qc, fq);
+        put(std::integral_constant<int, L::opp(q)>{}, fo);
       }
     });
-    bool solid = false;
-    if constexpr (MASK) {
-      solid = __ldg(a.mask + site) != 0;
-      msk[slot * ROWS * 32 + me] = solid ? 1 : 0;
-    }
-    solid_next = solid;
-    return solid;
-  };
-
-  auto shift_own = [&]() {
-    Fown[0] = Fnext[0];
-    Fown[1] = Fnext[1];
-    Fown[2] = Fnext[2];
-    inv2rho_own = inv2rho_next;
-    phi_own = phi_next;
-    solid_own = solid_next;
+    if constexpr (MASK) msk[m3 * SITES + me] = e.solid ? 1 : 0;
+    sol_new = e.solid;
+    return e.solid;
   };
 
   T red[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  SiteExtra<T, TWO> ex;
 
-  // ring: slot of plane z-1, z, z+1 (rotating)
-  int s_m = 0, s_0 = 1, s_p = 2;
-  bool any_m = stage(z0 - 1, s_m);
-  bool any_0 = stage(z0, s_0);
-  shift_own();
-  if constexpr (MASK) {
-    any_m = __syncthreads_or(any_m);
-    any_0 = __syncthreads_or(any_0);
+  if (me == 0) {
+    abort_flag = 0;
+    if constexpr (TMA) {
+      for (int s = 0; s < kRawStages; ++s) mbar_init(&bars[s], 1);
+      fence_mbar_init();
+    }
   }
-  for (int z = z0; z < z1; ++z) {
-    // own values of plane z were shifted in at the end of the previous iteration (or prologue)
-    const T Fo0 = Fown[0], Fo1 = Fown[1], Fo2 = Fown[2];
-    const T i2r = inv2rho_own;
-    const T phio = phi_own;
-    const bool solido = solid_own;
-    bool any_p = stage(z + 1, s_p);
+  __syncthreads();
+  if constexpr (TMA) {
+    if (me == 0) {
+      prefetch_tensormap(&tmap);
+      for (int p = pbase; p < pbase + kRawStages; ++p) issue(p);
+    }
+  }
+  int waited = pbase - 1;  // last plane whose TMA was waited for
+
+  // prologue: stage planes z0-1 and z0
+  load_extra(z0 - 1, ex);
+  if constexpr (TMA) {
+    wait_plane(z0 - 1);
+    waited = z0 - 1;
+  }
+  bool any_m = stage(z0 - 1, ex);
+  up_m1 = up_new;
+  sol_m1 = sol_new;
+  load_extra(z0, ex);
+  if constexpr (MASK)
+    any_m = __syncthreads_or(any_m);
+  else
+    __syncthreads();
+  if constexpr (TMA) {
+    if (me == 0) issue(z0 - 1 + kRawStages);
+    wait_plane(z0);
+    waited = z0;
+  }
+  bool any_0 = stage(z0, ex);
+  up_0 = up_new;
+  dn_0 = dn_new;
+  rest_0 = rest_new;
+  sol_0 = sol_new;
+  Fown[0] = Fnext[0];
+  Fown[1] = Fnext[1];
+  Fown[2] = Fnext[2];
+  i2r_own = i2r_next;
+  phi_own = phi_next;
+  load_extra(z0 + 1, ex);
+  if constexpr (MASK)
+    any_0 = __syncthreads_or(any_0);
+  else
+    __syncthreads();
+  if constexpr (TMA) {
+    if (me == 0) issue(z0 + kRawStages);
+  }
+
+  for (int z = z0; z < z1 && !abort_flag; ++z) {
+    if constexpr (TMA) {
+      wait_plane(z + 1);
+      waited = z + 1;
+    }
+    bool any_p = stage(z + 1, ex);
+    if (z + 2 <= z1) load_extra(z + 2, ex);  // in flight during the outputs of plane z
     if constexpr (MASK)
       any_p = __syncthreads_or(any_p);
     else
       __syncthreads();
-    if (outcol && !solido) {
-      const bool walls = MASK && (any_m || any_0 || any_p);
-      Accum<T> A = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-      const T* base0 = pop + s_0 * PLANE + me;
-      A.a0 = base0[REST * ROWS * 32];
-      static_for<Q>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        if constexpr (q != REST && q < L::opp(q)) {
-          constexpr int o = L::opp(q);
+    if constexpr (TMA) {
+      if (me == 0) issue(z + 1 + kRawStages);  // the stage of plane z+1 was consumed by everyone
+    }
+    if (outcol && !sol_0) {
+      const int par0 = (z + 6) & 1, par1 = (z + 7) & 1;
+      const int m3m = (z + 5) % 3, m30 = (z + 6) % 3, m3p = (z + 7) % 3;
+      // pull bases: group c_z = -1 from plane z+1, c_z = 0 from plane z, c_z = +1 from plane z-1
+      const T* P0 = ring + R::base(0) + par1 * D::gsize(0) * SITES + me;
+      const T* P1 = ring + R::base(1) + par0 * D::gsize(1) * SITES + me;
+      const T* P2 = ring + R::base(2) + m3m * D::gsize(2) * SITES + me;
+      auto gather = [&](auto walls_c) {
+        constexpr bool W = decltype(walls_c)::value;
+        const T* O0 = ring + R::base(0) + par0 * D::gsize(0) * SITES + me;  // own plane z
+        const T* O2 = ring + R::base(2) + m30 * D::gsize(2) * SITES + me;
+        const uint8_t* MM = msk + m3m * SITES + me;
+        const uint8_t* M0 = msk + m30 * SITES + me;
+        const uint8_t* MP = msk + m3p * SITES + me;
+        Accum<T> A = {rest_0, T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        auto pulled = [&](auto qc) -> T {
+          constexpr int q = decltype(qc)::value;
           constexpr int cx = L::cx(q), cy = L::cy(q), cz = L::cz(q);
-          // f_q pulled from x - c_q (plane z - cz), f_o from x + c_q (plane z + cz)
-          const int slot_q = cz > 0 ? s_m : (cz < 0 ? s_p : s_0);
-          const int slot_o = cz > 0 ? s_p : (cz < 0 ? s_m : s_0);
-          const int off_q = -cy * 32 - cx;
-          const int off_o = cy * 32 + cx;
-          T fq = pop[slot_q * PLANE + q * ROWS * 32 + me + off_q];
-          T fo = pop[slot_o * PLANE + o * ROWS * 32 + me + off_o];
-          if constexpr (MASK) {
-            if (walls) {
-              if (msk[slot_q * ROWS * 32 + me + off_q]) fq = base0[o * ROWS * 32];
-              if (msk[slot_o * ROWS * 32 + me + off_o]) fo = base0[q * ROWS * 32];
+          constexpr int g = D::group(q);
+          constexpr int off = D::gidx(q) * SITES - cy * 32 - cx;
+          T v = (g == 0 ? P0 : (g == 1 ? P1 : P2))[off];
+          if constexpr (W) {
+            const uint8_t* mk = cz > 0 ? MM : (cz < 0 ? MP : M0);
+            if (mk[-cy * 32 - cx]) {  // halfway bounce-back: own post-collision population of opp(q)
+              constexpr int o = L::opp(q);
+              constexpr int go = D::group(o);
+              v = (go == 0 ? O0 : (go == 1 ? P1 : O2))[D::gidx(o) * SITES];
             }
           }
-          accumulate_pair<cx, cy, cz, T>(A, fq, fo);
+          return v;
+        };
+        static_for<Q>([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          if constexpr (q != QREST && q < L::opp(q) && q != QUP && q != QDN) {
+            const T fq = pulled(qc);
+            const T fo = pulled(std::integral_constant<int, L::opp(q)>{});
+            accumulate_pair<L::cx(q), L::cy(q), L::cz(q), T>(A, fq, fo);
+          }
+        });
+        // axial pair: (0,0,+1) comes from the plane below, (0,0,-1) from the plane above
+        T fup = up_m1, fdn = dn_new;
+        if constexpr (W) {
+          if (sol_m1) fup = dn_0;
+          if (sol_new) fdn = up_0;
         }
-      });
+        accumulate_pair<0, 0, 1, T>(A, fup, fdn);
+        return A;
+      };
+      Accum<T> A;
+      if constexpr (MASK) {
+        if (any_m || any_0 || any_p)
+          A = gather(std::true_type{});
+        else
+          A = gather(std::false_type{});
+      } else {
+        A = gather(std::false_type{});
+      }
       // Eq. (corr): u = a1 + F/(2 rho), a2 = (sum c c f - cs2 a0 delta) + (u F + F u)/(2 rho)
-      const T ux = A.jx + Fo0 * i2r, uy = A.jy + Fo1 * i2r, uz = A.jz + Fo2 * i2r;
-      const T hx = Fo0 * i2r, hy = Fo1 * i2r, hz = Fo2 * i2r;
-      const T third = T(1) / T(3);
-      const T a0c = A.a0 * third;
+      const T i2r = i2r_own;
+      const T hx = Fown[0] * i2r, hy = Fown[1] * i2r, hz = Fown[2] * i2r;
+      const T ux = A.jx + hx, uy = A.jy + hy, uz = A.jz + hz;
+      const T a0c = A.a0 * (T(1) / T(3));
       const T nxx = (A.rxx - a0c) + T(2) * ux * hx - ux * ux;
       const T nyy = (A.ryy - a0c) + T(2) * uy * hy - uy * uy;
       const T nzz = (A.rzz - a0c) + T(2) * uz * hz - uz * uz;
       const T nxy = A.rxy + (ux * hy + hx * uy) - ux * uy;
       const T nxz = A.rxz + (ux * hz + hx * uz) - ux * uz;
       const T nyz = A.ryz + (uy * hz + hy * uz) - uy * uz;
-      const long long site = (long long)z * plane + col;
-      st_field<S, T>(dst, site, A.a0, a.sc.enc[0]);
-      st_field<S, T>(dst, N + site, ux, a.sc.enc[1]);
-      st_field<S, T>(dst, 2 * N + site, uy, a.sc.enc[1]);
-      st_field<S, T>(dst, 3 * N + site, uz, a.sc.enc[1]);
-      st_field<S, T>(dst, 4 * N + site, nxx, a.sc.enc[2]);
-      st_field<S, T>(dst, 5 * N + site, nyy, a.sc.enc[2]);
-      st_field<S, T>(dst, 6 * N + site, nzz, a.sc.enc[2]);
-      st_field<S, T>(dst, 7 * N + site, nxy, a.sc.enc[2]);
-      st_field<S, T>(dst, 8 * N + site, nxz, a.sc.enc[2]);
-      st_field<S, T>(dst, 9 * N + site, nyz, a.sc.enc[2]);
+      S* __restrict__ oz = dst + (long long)z * plane;
+      st_field<S, T>(oz, col, A.a0, a.sc.enc[0]);
+      st_field<S, T>(oz + N, col, ux, a.sc.enc[1]);
+      st_field<S, T>(oz + 2 * N, col, uy, a.sc.enc[1]);
+      st_field<S, T>(oz + 3 * N, col, uz, a.sc.enc[1]);
+      st_field<S, T>(oz + 4 * N, col, nxx, a.sc.enc[2]);
+      st_field<S, T>(oz + 5 * N, col, nyy, a.sc.enc[2]);
+      st_field<S, T>(oz + 6 * N, col, nzz, a.sc.enc[2]);
+      st_field<S, T>(oz + 7 * N, col, nxy, a.sc.enc[2]);
+      st_field<S, T>(oz + 8 * N, col, nxz, a.sc.enc[2]);
+      st_field<S, T>(oz + 9 * N, col, nyz, a.sc.enc[2]);
       const T uu = ux * ux + uy * uy + uz * uz;
       if (!(uu <= T(a.umax2))) atomicOr(a.flags, 1u);
       red[0] += A.a0;
       red[1] += ux;
       red[2] += uy;
       red[3] += uz;
-      red[4] += phio;
+      red[4] += phi_own;
       red[5] += uu;
     }
-    shift_own();
-    __syncthreads();
-    const int t = s_m;
-    s_m = s_0;
-    s_0 = s_p;
-    s_p = t;
+    // rotate the own-column carries to plane z+1
+    up_m1 = up_0;
+    up_0 = up_new;
+    dn_0 = dn_new;
+    rest_0 = rest_new;
+    sol_m1 = sol_0;
+    sol_0 = sol_new;
+    Fown[0] = Fnext[0];
+    Fown[1] = Fnext[1];
+    Fown[2] = Fnext[2];
+    i2r_own = i2r_next;
+    phi_own = phi_next;
     any_m = any_0;
     any_0 = any_p;
+    __syncthreads();
+  }
+
+  if constexpr (TMA) {
+    // after an aborted wait, let the copies still in flight land before the CTA exits (bounded)
+    if (abort_flag && me == 0) {
+      const int last_issued = min(z1, waited + kRawStages);
+      for (int p = waited; p <= last_issued; ++p) {
+        const int s = (p - pbase) % kRawStages;
+        mbar_wait_bounded(&bars[s], uint32_t((p - pbase) / kRawStages) & 1u, kWaitPolls);
+      }
+    }
   }
 
   if (a.partials != nullptr) {
-    double v[6];
+    // warp sums in the compute type, block and grid sums in FP64
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      v[k] = static_cast<double>(red[k]);
+      T v = red[k];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) red_s[row][k] = v[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red_s[row][k] = static_cast<double>(v);
     }
     __syncthreads();
     const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
@@ -410,7 +669,6 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS)
     __syncthreads();
     if (last) {
       __threadfence();
-      // fixed-shape tree over 512 slots per quantity, in the (now idle) ring buffer
       constexpr int NT = FwdTile<BY>::THREADS;
       double* tree = reinterpret_cast<double*>(smem_raw);
       for (int i = me; i < 6 * 512; i += NT) tree[i] = 0.0;

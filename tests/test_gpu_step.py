@@ -50,8 +50,11 @@ def run_oracle(lattice, storage, M0, force, field, mask, steps, tau):
 @pytest.mark.parametrize("lattice", [19, 27])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("case", ["periodic", "uniform_force", "walls_field"])
-def test_step_matches_oracle(lattice, storage, case):
-    shape = (11, 13, 37)  # 2 x-tiles (30 wide), 2-4 y-tiles, 2 z-chunks, ragged everywhere
+@pytest.mark.parametrize("nx", [37, 36])
+def test_step_matches_oracle(lattice, storage, case, nx):
+    """nx = 37: rows are not 16-byte multiples, planes load directly; nx = 36: TMA plane patches.
+    2 x-tiles (30 wide), 2-4 y-tiles, 2 z-chunks, ragged everywhere."""
+    shape = (11, 13, nx)
     M0, force, field, mask = make_case(case, shape, storage, seed=lattice)
     got, _ = run_gpu(lattice, storage, shape, M0, force, field, mask, 5, 0.7)
     want = run_oracle(lattice, storage, M0, force, field, mask, 5, 0.7)
@@ -60,7 +63,8 @@ def test_step_matches_oracle(lattice, storage, case):
 
 
 @pytest.mark.parametrize("lattice", [19, 27])
-@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 3, 2), (2, 1, 5), (3, 4, 1), (5, 2, 31), (9, 17, 30)])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 3, 2), (2, 1, 5), (3, 4, 1), (5, 2, 31), (9, 17, 30),
+                                   (1, 1, 2), (3, 5, 4), (2, 3, 8), (4, 9, 60), (3, 2, 62)])
 def test_degenerate_and_tile_edge_shapes(lattice, shape):
     M0, force, field, mask = make_case("uniform_force", shape, "f64", seed=3)
     got, _ = run_gpu(lattice, "f64", shape, M0, force, None, None, 3, 0.9)
@@ -82,11 +86,13 @@ def test_single_wall_site_and_fully_solid_rows(lattice):
 
 @pytest.mark.parametrize("lattice", [19, 27])
 @pytest.mark.parametrize("storage,bound", [("f16", 5e-3), ("bf16", 4e-2)])
-def test_16bit_storage_error_against_fp64(lattice, storage, bound):
+@pytest.mark.parametrize("nx", [34, 40])
+def test_16bit_storage_error_against_fp64(lattice, storage, bound, nx):
     """16-bit deviation storage with FP32 arithmetic: the error of p*, u and A against the FP64
-    oracle stays within the storage rounding accumulated over the steps (stated, not exact)."""
-    shape = (10, 12, 34)
-    M0 = synth.taylor_green_perturbed((10, 12, 34), 0.04, 0.6, 0.01, seed=5)
+    oracle stays within the storage rounding accumulated over the steps (stated, not exact).
+    nx = 40 takes the TMA path (80-byte rows), nx = 34 the direct loads."""
+    shape = (10, 12, nx)
+    M0 = synth.taylor_green_perturbed(shape, 0.04, 0.6, 0.01, seed=5)
     got, _ = run_gpu(lattice, storage, shape, M0, (0.0, 0.0, 0.0), None, None, 10, 0.6)
     want = run_oracle(lattice, "f64", M0, (0.0, 0.0, 0.0), None, None, 10, 0.6)
     err = group_errors(got, want)
@@ -137,7 +143,7 @@ def test_host_buffers_round_trip_and_match_device_path():
     shape = (6, 10, 35)
     M0 = synth.random_moments(shape, seed=30)
     a = Solver(shape, lattice=19, tau=0.7, storage="f32")
-    a.set_moments(M0.cuda())
+    a.set_moments(M0.to(torch.float32).cuda())
     a.step(2)
     b = Solver(shape, lattice=19, tau=0.7, storage="f32")
     b.set_moments(M0.to(torch.float32).pin_memory())
@@ -185,3 +191,36 @@ def test_step_state_equals_step():
     c = s.new_state()
     s.copy_state(c)
     assert torch.equal(b, c)
+
+
+@pytest.mark.parametrize("lattice", [19, 27])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("walls", [False, True])
+def test_tma_and_direct_loads_agree(lattice, storage, walls, monkeypatch):
+    """The TMA-staged and the directly loaded kernels read the same values. FP32/FP64 states agree
+    bit for bit; with 16-bit storage the two instantiations may fuse multiply-adds differently, so
+    a stored value may differ by one unit in the last place of the storage type."""
+    shape = (9, 19, 64)
+    M0 = synth.random_moments(shape, seed=40)
+    mask = synth.channel_walls(shape) | synth.random_mask(shape, 0.05, seed=41) if walls else None
+    outs = []
+    for no_tma in (False, True):
+        if no_tma:
+            monkeypatch.setenv("LBF_NO_TMA", "1")
+        s = Solver(shape, lattice=lattice, tau=0.6, storage=storage, force=(1e-5, 0.0, 2e-5), mask=mask)
+        s.set_moments(M0.cuda())
+        s.step(4)
+        st = s.new_state()
+        s.copy_state(st)
+        outs.append((st.cpu(), s.reduce()))
+    if storage in ("f32", "f64"):
+        assert torch.equal(outs[0][0], outs[1][0])
+        assert outs[0][1] == outs[1][1]
+    else:
+        # adjacent 16-bit values of one sign differ by one in their bit patterns
+        ia = outs[0][0].view(torch.int16).int()
+        ib = outs[1][0].view(torch.int16).int()
+        assert int((ia - ib).abs().max()) <= 1
+        assert (ia != ib).float().mean().item() < 1e-3
+        for x, y in zip(outs[0][1], outs[1][1]):
+            assert abs(x - y) <= 1e-3 * max(abs(y), 1e-12)
