@@ -141,6 +141,28 @@ lbf_status lbf_step_state(lbf_ctx* ctx, const void* src, void* dst);
 lbf_status lbf_adjoint_step(lbf_ctx* ctx, const void* state_t, const void* state_t1, const void* lambda_in,
                             void* lambda_out, double* grad_force);
 
+/* One fused single-component step without any device allocation, for callers that cannot
+   allocate device memory: code running under another framework's memory pool or a fixed memory
+   plan, or an embedder that only receives device buffers from elsewhere, cannot call cudaMalloc
+   and so cannot provide the workspace lbf_create needs. (The paper has no counterpart; this is a
+   deployment entry point.)
+   params: lattice, nx/ny/nz, storage (LBF_F32 or LBF_F64 only), tau, force, force_field and stream
+   as for lbf_create; params->mask and the two-component fields are not used.
+   src, dst: caller DEVICE buffers of 10*nx*ny*nz values in the internal state layout (the bytes
+   lbf_copy_state produces; for FP32/FP64 storage the tensor fields hold a2 - u u), src != dst.
+   mask_device: optional DEVICE mask, nx*ny*nz bytes, nonzero = solid (solid sites of dst are not
+   written). sums_device: optional DEVICE output of 6 doubles, the sums of lbf_reduce for dst.
+   The library keeps the per-block partial sums, a block counter and the error flags in one static
+   device array of 1 MiB + 256 bytes per GPU that loads it (held until the process exits), enough
+   for 16384 CTAs: ceil(nx/30) * ceil(ny/8) (FP32; ny/4 for FP64) must not exceed 16384, else
+   LBF_EINVAL. The first call on a device looks up that array's device address; make it before any
+   stream capture. Every call clears the counter and flags it needs (cudaMemsetAsync, which does not
+   allocate). All calls share the array: calls that can overlap on the GPU (other streams, other
+   host threads) race on it; calls ordered on one stream are safe. Instability is not reported
+   (no context to hold it); the u.u sum shows it. Asynchronous on params->stream. */
+lbf_status lbf_step_static(const lbf_params* params, const void* src, void* dst, const uint8_t* mask_device,
+                           double* sums_device);
+
 /* Releases the host-side context. The workspace stays owned by the caller. */
 lbf_status lbf_destroy(lbf_ctx* ctx);
 

@@ -14,8 +14,8 @@ LBF_OK, LBF_EINVAL, LBF_ENOMEM, LBF_ECUDA, LBF_EUNSTABLE, LBF_EINTERNAL, LBF_ENO
 # every symbol declared in include/lbf.h
 EXPORTS = ("lbf_workspace_bytes", "lbf_validate", "lbf_create", "lbf_set_moments", "lbf_step", "lbf_moments",
            "lbf_reduce", "lbf_synchronize", "lbf_state_bytes", "lbf_copy_state", "lbf_load_state",
-           "lbf_step_state", "lbf_adjoint_step", "lbf_destroy", "lbf_status_string", "lbf_last_error",
-           "lbf_version")
+           "lbf_step_state", "lbf_adjoint_step", "lbf_step_static", "lbf_destroy", "lbf_status_string",
+           "lbf_last_error", "lbf_version")
 
 
 class lbf_params(ctypes.Structure):
@@ -62,6 +62,7 @@ def load_library(path=LIB_PATH):
         "lbf_load_state": (I, [VP, VP]),
         "lbf_step_state": (I, [VP, VP, VP]),
         "lbf_adjoint_step": (I, [VP, VP, VP, VP, VP, VP]),
+        "lbf_step_static": (I, [P(lbf_params), VP, VP, VP, VP]),
         "lbf_destroy": (I, [VP]),
         "lbf_status_string": (ctypes.c_char_p, [I]),
         "lbf_last_error": (ctypes.c_char_p, []),
@@ -141,6 +142,12 @@ def lbf_adjoint_step(ctx, state_t_ptr, state_t1_ptr, lam_in_ptr, lam_out_ptr, gr
     _check(load_library().lbf_adjoint_step(ctx, ctypes.c_void_p(state_t_ptr), ctypes.c_void_p(state_t1_ptr),
                                            ctypes.c_void_p(lam_in_ptr), ctypes.c_void_p(lam_out_ptr),
                                            ctypes.c_void_p(grad_force_ptr)))
+
+
+def lbf_step_static(params, src_ptr, dst_ptr, mask_ptr=None, sums_ptr=None):
+    """One step from src to dst with no device allocation (static scratch in the library)."""
+    _check(load_library().lbf_step_static(ctypes.byref(params), ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr),
+                                          ctypes.c_void_p(mask_ptr), ctypes.c_void_p(sums_ptr)))
 
 
 def lbf_destroy(ctx):

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbf.so")
-SOURCES = ["api.cu", "kernels_d3q19.cu", "kernels_d3q27.cu"]
+SOURCES = ["api.cu", "kernels_d3q19.cu", "kernels_d3q27.cu", "static_step.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-O2", "-I", os.path.join(ROOT, "include")]

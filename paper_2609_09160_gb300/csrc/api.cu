@@ -455,6 +455,9 @@ void host_absmax(const T* src, long long N, double m[3]) {
 
 }  // namespace
 
+// lets the other translation units of the library report through lbf_last_error()
+void lbf_internal_set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 extern "C" {
 
 int lbf_version(void) { return 1; }
