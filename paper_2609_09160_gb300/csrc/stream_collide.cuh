@@ -230,11 +230,16 @@ constexpr size_t raw_stage_bytes() {
   return (size_t(10) * ROWS * TmaBox<S>::BX * sizeof(S) + 127) / 128 * 128;
 }
 
+// elements (ring) / bytes (solid flags) of slack on each side; the edge lanes of an output row
+// read at most 33 entries before or after their row
+constexpr int kRingPad = 40;
+
 template <class L, class S, int BY, bool MASK, bool TMA>
 constexpr size_t fwd_smem_bytes() {
   using T = typename ComputeOf<S>::type;
   const size_t raw = TMA ? 128 + size_t(kRawStages) * raw_stage_bytes<S, BY + 2>() : 0;
-  return raw + size_t(GroupRing<L, BY + 2>::VALUES) * sizeof(T) + (MASK ? size_t(3) * (BY + 2) * 32 : 0);
+  return raw + size_t(GroupRing<L, BY + 2>::VALUES + 2 * kRingPad) * sizeof(T) +
+         (MASK ? size_t(3) * (BY + 2) * 32 + 2 * kRingPad : 0);
 }
 
 // per-site inputs other than the 10 stored fields, prefetched one plane ahead
@@ -271,16 +276,19 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   constexpr int STAGE_ELEMS = 10 * ROWS * BX;                                  // one box
   constexpr int STAGE_STRIDE = int(raw_stage_bytes<S, ROWS>() / sizeof(S));   // padded stage
   constexpr size_t RAW_BYTES = TMA ? 128 + size_t(kRawStages) * raw_stage_bytes<S, ROWS>() : 0;
+  constexpr int G0 = D::gsize(0) * SITES, G1 = D::gsize(1) * SITES, G2 = D::gsize(2) * SITES;
   static_assert(fwd_smem_bytes<L, S, BY, MASK, TMA>() >= 6 * 512 * sizeof(double), "smem too small for the final tree");
   static_assert(FwdTile<BY>::THREADS <= 512, "final tree assumes <= 512 threads");
+  static_assert(kRawStages == 2, "plane parities below assume two raw stages");
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   S* rawst = reinterpret_cast<S*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
-  T* ring = reinterpret_cast<T*>(smem_raw + RAW_BYTES);
-  uint8_t* msk = reinterpret_cast<uint8_t*>(smem_raw + RAW_BYTES + size_t(R::VALUES) * sizeof(T));
+  // population ring and solid-flag ring, each with kRingPad elements of slack on both sides: the
+  // edge lanes of an output row read one element beyond their row (results discarded)
+  T* ring = reinterpret_cast<T*>(smem_raw + RAW_BYTES) + kRingPad;
+  uint8_t* msk = reinterpret_cast<uint8_t*>(ring + R::VALUES + kRingPad) + kRingPad;
   __shared__ __align__(8) uint64_t bars[kRawStages];
   __shared__ int abort_flag;
-  __shared__ double red_s[ROWS][6];
 
   const S* __restrict__ src = static_cast<const S*>(a.src);
   S* __restrict__ dst = static_cast<S*>(a.dst);
@@ -292,7 +300,8 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   const int gy = blockIdx.y * BY - 1 + row;
   const int sx = ((gx % a.nx) + a.nx) % a.nx;
   const int sy = ((gy % a.ny) + a.ny) % a.ny;
-  const bool outcol = lane >= 1 && lane <= FwdTile<BY>::XOUT && row >= 1 && row <= BY && gx < a.nx && gy < a.ny;
+  const bool out_row = row >= 1 && row <= BY;  // warp-uniform
+  const bool outcol = out_row && lane >= 1 && lane <= FwdTile<BY>::XOUT && gx < a.nx && gy < a.ny;
   const bool inbox = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;  // TMA delivers this site
   const bool needed = gx <= a.nx && gy <= a.ny;                      // read by some output
   const int xa = ((x0 - 1 + AL) / AL - 1) * AL;                      // floor to AL; x0 - 1 >= -1
@@ -306,12 +315,14 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   const T one_m_omega = T(1) - T(a.omega);
   const T Fu0 = T(a.force[0]), Fu1 = T(a.force[1]), Fu2 = T(a.force[2]);
   const bool has_field = ffield != nullptr;
-  const int pbase = z0 - 1;  // first plane of this chunk's window (planes z0-1 .. z1 are staged)
+  // planes of the chunk window are numbered r = p - (z0 - 1) >= 0: raw stage and the two-slot ring
+  // groups use r & 1, the three-slot group and the solid flags rotate through three slots
+  const int pbase = z0 - 1;
+  const S* raw_me = rawst + row * BX + lane + xoff;  // this thread's site in stage 0
 
-  // -- TMA issue / wait (plane p lives in stage (p - pbase) % kRawStages) ---------------------
   auto issue = [&](int p) {  // elected thread only
     if (p > z1 || abort_flag) return;
-    const int s = (p - pbase) % kRawStages;
+    const int s = (p - pbase) & 1;
     S* dstp = rawst + s * STAGE_STRIDE;
     if ((smem_u32(dstp) & 127u) != 0u) {  // never issue a copy the hardware would reject
       atomicOr(a.flags, 4u);
@@ -324,8 +335,8 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   };
   auto wait_plane = [&](int p) {
     if (abort_flag) return;
-    const int s = (p - pbase) % kRawStages;
-    const uint32_t parity = uint32_t((p - pbase) / kRawStages) & 1u;
+    const int s = (p - pbase) & 1;
+    const uint32_t parity = uint32_t((p - pbase) >> 1) & 1u;
     if (!mbar_wait_bounded(&bars[s], parity, kWaitPolls)) {
       atomicOr(a.flags, 2u);
       abort_flag = 1;
@@ -365,10 +376,10 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     else e.solid = false;
   };
 
-  // the 10 stored values of this thread's site in plane p
-  auto read_raw = [&](int p, T (&m)[10]) {
+  // the 10 stored values of this thread's site in plane p (raw stage `st` when staged by TMA)
+  auto read_raw = [&](int p, int st, T (&m)[10]) {
     if (TMA && inbox) {
-      const S* b = rawst + ((p - pbase) % kRawStages) * STAGE_STRIDE + row * BX + lane + xoff;
+      const S* b = raw_me + st * STAGE_STRIDE;
 #pragma unroll
       for (int k = 0; k < 10; ++k) {
         const float dec = k == 0 ? a.sc.dec[0] : (k < 4 ? a.sc.dec[1] : a.sc.dec[2]);
@@ -398,11 +409,17 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   T up_m1 = T(0), up_0 = T(0), dn_0 = T(0), rest_0 = T(0);
   T up_new = T(0), dn_new = T(0), rest_new = T(0);
   bool sol_m1 = false, sol_0 = false, sol_new = false;
+  // three-slot ring offsets (elements of the c_z = +1 group, bytes of the solid flags) of the
+  // planes z-1, z, z+1; they rotate by one slot per plane
+  int g2m = 0, g20 = G2, g2p = 2 * G2;
+  int mkm = 0, mk0 = SITES, mkp = 2 * SITES;
 
   // -- staging: post-collision populations of plane p into the ring ----------------------------
-  auto stage = [&](int p, const SiteExtra<T, TWO>& e) -> bool {
+  // par: (p - pbase) & 1 (compile time); g2, mk: the three-slot offsets of plane p
+  auto stage = [&](auto par_c, int p, int g2, int mk, const SiteExtra<T, TWO>& e) -> bool {
+    constexpr int par = decltype(par_c)::value;
     T m[10];
-    read_raw(p, m);
+    read_raw(p, par, m);
     T inv2rho = T(0.5), omm = one_m_omega;
     if constexpr (TWO) {
       const T rho = T(a.rho_l) + e.phi_o * T(a.rho_h - a.rho_l);
@@ -423,10 +440,9 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     }
     const PostColl<T> P = post_collision<T>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9], e.F[0],
                                             e.F[1], e.F[2], inv2rho, omm);
-    const int par = (p + 6) & 1, m3 = (p + 6) % 3;
-    T* g0 = ring + R::base(0) + par * D::gsize(0) * SITES + me;
-    T* g1 = ring + R::base(1) + par * D::gsize(1) * SITES + me;
-    T* g2 = ring + R::base(2) + m3 * D::gsize(2) * SITES + me;
+    T* w0 = ring + R::base(0) + par * G0 + me;
+    T* w1 = ring + R::base(1) + par * G1 + me;
+    T* w2 = ring + R::base(2) + g2 + me;
     auto put = [&](auto qc, T v) {
       constexpr int q = decltype(qc)::value;
       if constexpr (q == QUP) {
@@ -435,7 +451,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
         dn_new = v;
       } else {
         constexpr int g = D::group(q);
-        T* b = g == 0 ? g0 : (g == 1 ? g1 : g2);
+        T* b = g == 0 ? w0 : (g == 1 ? w1 : w2);
         b[D::gidx(q) * SITES] = v;
       }
     };
@@ -450,7 +466,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
         put(std::integral_constant<int, L::opp(q)>{}, fo);
       }
     });
-    if constexpr (MASK) msk[m3 * SITES + me] = e.solid ? 1 : 0;
+    if constexpr (MASK) msk[mk + me] = e.solid ? 1 : 0;
     sol_new = e.solid;
     return e.solid;
   };
@@ -465,6 +481,13 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
       fence_mbar_init();
     }
   }
+  if constexpr (MASK) {
+    // solid-flag padding read by the edge lanes: keep it defined
+    for (int i = me; i < kRingPad; i += FwdTile<BY>::THREADS) {
+      msk[-kRingPad + i] = 0;
+      msk[3 * SITES + i] = 0;
+    }
+  }
   __syncthreads();
   if constexpr (TMA) {
     if (me == 0) {
@@ -474,13 +497,13 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   }
   int waited = pbase - 1;  // last plane whose TMA was waited for
 
-  // prologue: stage planes z0-1 and z0
+  // prologue: stage planes z0-1 (r = 0) and z0 (r = 1)
   load_extra(z0 - 1, ex);
   if constexpr (TMA) {
     wait_plane(z0 - 1);
     waited = z0 - 1;
   }
-  bool any_m = stage(z0 - 1, ex);
+  bool any_m = stage(std::integral_constant<int, 0>{}, z0 - 1, g2m, mkm, ex);
   up_m1 = up_new;
   sol_m1 = sol_new;
   load_extra(z0, ex);
@@ -493,7 +516,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     wait_plane(z0);
     waited = z0;
   }
-  bool any_0 = stage(z0, ex);
+  bool any_0 = stage(std::integral_constant<int, 1>{}, z0, g20, mk0, ex);
   up_0 = up_new;
   dn_0 = dn_new;
   rest_0 = rest_new;
@@ -512,12 +535,14 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     if (me == 0) issue(z0 + kRawStages);
   }
 
-  for (int z = z0; z < z1 && !abort_flag; ++z) {
+  // one plane: stage z+1, outputs of z. PAR = (z - z0) & 1 at compile time
+  auto iteration = [&](auto par_c, int z) {
+    constexpr int PAR = decltype(par_c)::value;
     if constexpr (TMA) {
       wait_plane(z + 1);
       waited = z + 1;
     }
-    bool any_p = stage(z + 1, ex);
+    bool any_p = stage(std::integral_constant<int, PAR>{}, z + 1, g2p, mkp, ex);
     if (z + 2 <= z1) load_extra(z + 2, ex);  // in flight during the outputs of plane z
     if constexpr (MASK)
       any_p = __syncthreads_or(any_p);
@@ -526,20 +551,18 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     if constexpr (TMA) {
       if (me == 0) issue(z + 1 + kRawStages);  // the stage of plane z+1 was consumed by everyone
     }
-    if (outcol && !sol_0) {
-      const int par0 = (z + 6) & 1, par1 = (z + 7) & 1;
-      const int m3m = (z + 5) % 3, m30 = (z + 6) % 3, m3p = (z + 7) % 3;
+    if (out_row) {
       // pull bases: group c_z = -1 from plane z+1, c_z = 0 from plane z, c_z = +1 from plane z-1
-      const T* P0 = ring + R::base(0) + par1 * D::gsize(0) * SITES + me;
-      const T* P1 = ring + R::base(1) + par0 * D::gsize(1) * SITES + me;
-      const T* P2 = ring + R::base(2) + m3m * D::gsize(2) * SITES + me;
+      const T* P0 = ring + R::base(0) + PAR * G0 + me;
+      const T* P1 = ring + R::base(1) + (PAR ^ 1) * G1 + me;
+      const T* P2 = ring + R::base(2) + g2m + me;
       auto gather = [&](auto walls_c) {
         constexpr bool W = decltype(walls_c)::value;
-        const T* O0 = ring + R::base(0) + par0 * D::gsize(0) * SITES + me;  // own plane z
-        const T* O2 = ring + R::base(2) + m30 * D::gsize(2) * SITES + me;
-        const uint8_t* MM = msk + m3m * SITES + me;
-        const uint8_t* M0 = msk + m30 * SITES + me;
-        const uint8_t* MP = msk + m3p * SITES + me;
+        const T* O0 = ring + R::base(0) + (PAR ^ 1) * G0 + me;  // own site, plane z
+        const T* O2 = ring + R::base(2) + g20 + me;
+        const uint8_t* MM = msk + mkm + me;
+        const uint8_t* M0 = msk + mk0 + me;
+        const uint8_t* MP = msk + mkp + me;
         Accum<T> A = {rest_0, T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         auto pulled = [&](auto qc) -> T {
           constexpr int q = decltype(qc)::value;
@@ -594,27 +617,29 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
       const T nxy = A.rxy + (ux * hy + hx * uy) - ux * uy;
       const T nxz = A.rxz + (ux * hz + hx * uz) - ux * uz;
       const T nyz = A.ryz + (uy * hz + hy * uz) - uy * uz;
-      S* __restrict__ oz = dst + (long long)z * plane;
-      st_field<S, T>(oz, col, A.a0, a.sc.enc[0]);
-      st_field<S, T>(oz + N, col, ux, a.sc.enc[1]);
-      st_field<S, T>(oz + 2 * N, col, uy, a.sc.enc[1]);
-      st_field<S, T>(oz + 3 * N, col, uz, a.sc.enc[1]);
-      st_field<S, T>(oz + 4 * N, col, nxx, a.sc.enc[2]);
-      st_field<S, T>(oz + 5 * N, col, nyy, a.sc.enc[2]);
-      st_field<S, T>(oz + 6 * N, col, nzz, a.sc.enc[2]);
-      st_field<S, T>(oz + 7 * N, col, nxy, a.sc.enc[2]);
-      st_field<S, T>(oz + 8 * N, col, nxz, a.sc.enc[2]);
-      st_field<S, T>(oz + 9 * N, col, nyz, a.sc.enc[2]);
       const T uu = ux * ux + uy * uy + uz * uz;
-      if (!(uu <= T(a.umax2))) atomicOr(a.flags, 1u);
-      red[0] += A.a0;
-      red[1] += ux;
-      red[2] += uy;
-      red[3] += uz;
-      red[4] += phi_own;
-      red[5] += uu;
+      if (outcol && !sol_0) {
+        const long long zc = (long long)z * plane + col;
+        st_field<S, T>(dst, zc, A.a0, a.sc.enc[0]);
+        st_field<S, T>(dst + N, zc, ux, a.sc.enc[1]);
+        st_field<S, T>(dst + 2 * N, zc, uy, a.sc.enc[1]);
+        st_field<S, T>(dst + 3 * N, zc, uz, a.sc.enc[1]);
+        st_field<S, T>(dst + 4 * N, zc, nxx, a.sc.enc[2]);
+        st_field<S, T>(dst + 5 * N, zc, nyy, a.sc.enc[2]);
+        st_field<S, T>(dst + 6 * N, zc, nzz, a.sc.enc[2]);
+        st_field<S, T>(dst + 7 * N, zc, nxy, a.sc.enc[2]);
+        st_field<S, T>(dst + 8 * N, zc, nxz, a.sc.enc[2]);
+        st_field<S, T>(dst + 9 * N, zc, nyz, a.sc.enc[2]);
+        if (!(uu <= T(a.umax2))) atomicOr(a.flags, 1u);
+        red[0] += A.a0;
+        red[1] += ux;
+        red[2] += uy;
+        red[3] += uz;
+        red[4] += phi_own;
+        red[5] += uu;
+      }
     }
-    // rotate the own-column carries to plane z+1
+    // rotate the own-column carries and the three-slot offsets to plane z+1
     up_m1 = up_0;
     up_0 = up_new;
     dn_0 = dn_new;
@@ -628,7 +653,20 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     phi_own = phi_next;
     any_m = any_0;
     any_0 = any_p;
+    const int g2t = g2m;
+    g2m = g20;
+    g20 = g2p;
+    g2p = g2t;
+    const int mkt = mkm;
+    mkm = mk0;
+    mk0 = mkp;
+    mkp = mkt;
     __syncthreads();
+  };
+
+  for (int z = z0; z < z1 && !abort_flag; z += 2) {
+    iteration(std::integral_constant<int, 0>{}, z);
+    if (z + 1 < z1 && !abort_flag) iteration(std::integral_constant<int, 1>{}, z + 1);
   }
 
   if constexpr (TMA) {
@@ -636,26 +674,27 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     if (abort_flag && me == 0) {
       const int last_issued = min(z1, waited + kRawStages);
       for (int p = waited; p <= last_issued; ++p) {
-        const int s = (p - pbase) % kRawStages;
-        mbar_wait_bounded(&bars[s], uint32_t((p - pbase) / kRawStages) & 1u, kWaitPolls);
+        const int s = (p - pbase) & 1;
+        mbar_wait_bounded(&bars[s], uint32_t((p - pbase) >> 1) & 1u, kWaitPolls);
       }
     }
   }
 
   if (a.partials != nullptr) {
-    // warp sums in the compute type, block and grid sums in FP64
+    // warp sums in the compute type, block and grid sums in FP64 (scratch: the idle ring)
+    double* red_s = reinterpret_cast<double*>(smem_raw + RAW_BYTES);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       T v = red[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red_s[row][k] = static_cast<double>(v);
+      if (lane == 0) red_s[row * 6 + k] = static_cast<double>(v);
     }
     __syncthreads();
     const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
     if (me < 6) {
       double s = 0.0;
-      for (int r = 0; r < ROWS; ++r) s += red_s[r][me];
+      for (int r = 0; r < ROWS; ++r) s += red_s[r * 6 + me];
       const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
       a.partials[b * 8 + me] = s;
     }

@@ -197,9 +197,10 @@ def test_step_state_equals_step():
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
 @pytest.mark.parametrize("walls", [False, True])
 def test_tma_and_direct_loads_agree(lattice, storage, walls, monkeypatch):
-    """The TMA-staged and the directly loaded kernels read the same values. FP32/FP64 states agree
-    bit for bit; with 16-bit storage the two instantiations may fuse multiply-adds differently, so
-    a stored value may differ by one unit in the last place of the storage type."""
+    """The TMA-staged and the directly loaded kernels read the same values and run the same
+    arithmetic, compiled separately: the compiler may group multiply-adds differently in the two
+    variants (each is deterministic run to run), so one step from the same state must agree to the
+    rounding of the storage type - a few units in the last place of FP32/FP64, one of FP16/BF16."""
     shape = (9, 19, 64)
     M0 = synth.random_moments(shape, seed=40)
     mask = synth.channel_walls(shape) | synth.random_mask(shape, 0.05, seed=41) if walls else None
@@ -209,18 +210,18 @@ def test_tma_and_direct_loads_agree(lattice, storage, walls, monkeypatch):
             monkeypatch.setenv("LBF_NO_TMA", "1")
         s = Solver(shape, lattice=lattice, tau=0.6, storage=storage, force=(1e-5, 0.0, 2e-5), mask=mask)
         s.set_moments(M0.cuda())
-        s.step(4)
+        s.step(1)
         st = s.new_state()
         s.copy_state(st)
-        outs.append((st.cpu(), s.reduce()))
+        outs.append((st.cpu(), s.moments().cpu(), s.reduce()))
     if storage in ("f32", "f64"):
-        assert torch.equal(outs[0][0], outs[1][0])
-        assert outs[0][1] == outs[1][1]
+        err = group_errors(outs[0][1], outs[1][1])
+        assert max(err.values()) < (1e-6 if storage == "f32" else 1e-14), err
     else:
         # adjacent 16-bit values of one sign differ by one in their bit patterns
         ia = outs[0][0].view(torch.int16).int()
         ib = outs[1][0].view(torch.int16).int()
         assert int((ia - ib).abs().max()) <= 1
         assert (ia != ib).float().mean().item() < 1e-3
-        for x, y in zip(outs[0][1], outs[1][1]):
-            assert abs(x - y) <= 1e-3 * max(abs(y), 1e-12)
+    for x, y in zip(outs[0][2], outs[1][2]):
+        assert abs(x - y) <= 1e-3 * max(abs(y), 1e-12)
