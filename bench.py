@@ -148,6 +148,8 @@ WORKLOADS = {
     "tg512_d3q27_bf16": (27, "bf16", "tg512"),
     "tg512_d3q19_f32": (19, "f32", "tg512"),
     "tg512_d3q19_f16": (19, "f16", "tg512"),
+    "droplet128": (19, "f32", "droplet"),
+    "adjoint128": (19, "f32", "adjoint"),
 }
 
 
@@ -156,6 +158,8 @@ def workload_solver(torch, device, key):
     lattice, storage, kind = WORKLOADS[key]
     if kind == "channel":
         return channel_solver(torch, device, storage, lattice)
+    if kind == "droplet":
+        return droplet_solver(torch, device)
     import synth
     from paper_2609_09160_gb300 import Solver
 
@@ -163,6 +167,51 @@ def workload_solver(torch, device, key):
     M0 = synth.taylor_green_perturbed(n, 0.04, 0.55, 0.01, seed=3, dtype=torch.float32, device=device)
     s = Solver((n, n, n), lattice=lattice, tau=0.55, storage=storage, device=device)
     return s, M0, None
+
+
+def droplet_solver(torch, device, n=128):
+    """Two-component static droplet: R = 20, W = 4, sigma = 0.03, D = 0.1, equal densities, tau = 1."""
+    import synth
+    from paper_2609_09160_gb300 import Solver
+
+    shape = (n, n, n)
+    s = Solver(shape, lattice=19, storage="f32", device=device,
+               two_component=dict(rho_l=1.0, rho_h=1.0, tau_l=1.0, tau_h=1.0, sigma=0.03, width=4.0, diffusivity=0.1))
+    phi0 = synth.droplet(shape, 20.0, 4.0, dtype=torch.float32, device=device)
+    M0 = torch.zeros((10,) + shape, dtype=torch.float32, device=device)
+    s._phi0 = phi0
+    return s, M0, None
+
+
+def adjoint_rollout(torch, device, T=500, K=50, reps=2):
+    """Config-5 rollout: 128(x) x 64(y) x 64(z) channel, per-site force N(0, 1e-12) on the fluid,
+    loss = mean |u(T) - u_target|^2, checkpoints every K steps. Returns (forward s, backward s)."""
+    import synth
+    from paper_2609_09160_gb300 import Solver, rollout
+
+    shape = (64, 64, 128)
+    mask = synth.channel_walls(shape)
+    F = synth.random_field(shape, 1e-6, seed=70, mask=mask).to(device=device, dtype=torch.float32)
+    F.requires_grad_(True)
+    u_tgt = synth.random_field(shape, 1e-4, seed=71).to(device=device, dtype=torch.float32)
+    fluid = (~mask).to(device=device, dtype=torch.float32)
+    s = Solver(shape, lattice=19, tau=0.9, storage="f32", force_field=F.detach(), mask=mask, device=device)
+    M0 = torch.zeros((10,) + shape, dtype=torch.float32, device=device)
+    times = []
+    for _ in range(reps):  # the first repetition warms up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        MT = rollout(F, M0, s, T, K)
+        d = (MT[1:4] - u_tgt) * fluid
+        L = (d * d).sum() / fluid.sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        L.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        F.grad = None
+        times.append((t1 - t0, t2 - t1))
+    return times[-1], s.N
 
 
 def channel_solver(torch, device, storage="f32", lattice=19, shape=SHAPE):
@@ -272,15 +321,12 @@ def extras(torch, device, quick):
     torch.cuda.empty_cache()
 
     # two-component droplet, 128^3, R = 20, equal densities, tau = 1 (config of the Laplace test)
-    shape = (128, 128, 128)
-    phi0 = synth.droplet(shape, 20.0, 4.0, dtype=torch.float32, device=device)
-    s = Solver(shape, lattice=19, storage="f32", device=device,
-               two_component=dict(rho_l=1.0, rho_h=1.0, tau_l=1.0, tau_h=1.0, sigma=0.03, width=4.0, diffusivity=0.1))
-    s.set_moments(torch.zeros((10,) + shape, dtype=torch.float32, device=device), phi0)
+    s, M0, _ = droplet_solver(torch, device)
+    s.set_moments(M0, s._phi0)
     r = rate(s, 50 if quick else 200, 5, algorithmic_bytes("f32") + 4 * (1 + 1 + 3 + 3) + 4 * 3 * 2)
     r["note"] = "3 kernels per step (phase field advance, forces, fused LB)"
     out["droplet128_d3q19_f32"] = r
-    del s
+    del s, M0
 
     # FP64 parity mode: 32^3 Taylor-Green (launch-latency bound at this size)
     s = Solver((32, 32, 32), lattice=19, tau=0.8, storage="f64", device=device)
@@ -289,29 +335,11 @@ def extras(torch, device, quick):
     del s
 
     # adjoint / forward time ratio: 128x64x64 channel, per-site force, 500 steps, checkpoints every 50
-    shape = (64, 64, 128)
-    mask = synth.channel_walls(shape)
-    F = synth.random_field(shape, 1e-6, seed=70, mask=mask).to(device=device, dtype=torch.float32)
-    F.requires_grad_(True)
-    u_tgt = synth.random_field(shape, 1e-4, seed=71).to(device=device, dtype=torch.float32)
-    fluid = (~mask).to(device=device, dtype=torch.float32)
-    s = Solver(shape, lattice=19, tau=0.9, storage="f32", force_field=F.detach(), mask=mask, device=device)
-    M0 = torch.zeros((10,) + shape, dtype=torch.float32, device=device)
     T = 100 if quick else 500
-    for rep in range(2):  # first repetition warms up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        MT = rollout(F, M0, s, T, 50)
-        d = (MT[1:4] - u_tgt) * fluid
-        L = (d * d).sum() / fluid.sum()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        L.backward()
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        F.grad = None
-    out["adjoint_128x64x64_d3q19_f32"] = {"forward_s": round(t1 - t0, 4), "backward_s": round(t2 - t1, 4),
-                                          "ratio": round((t2 - t1) / (t1 - t0), 3), "steps": T, "checkpoint_every": 50}
+    (tf, tb), n = adjoint_rollout(torch, device, T=T)
+    out["adjoint_128x64x64_d3q19_f32"] = {"forward_s": round(tf, 4), "backward_s": round(tb, 4),
+                                          "ratio": round(tb / tf, 3), "steps": T, "checkpoint_every": 50,
+                                          "forward_MLUPS": round(n * T / tf / 1e6, 1)}
     return out
 
 
@@ -332,8 +360,18 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         barrier = dist.barrier
+    if WORKLOADS[args.workload][2] == "adjoint":
+        (tf, tb), n = adjoint_rollout(torch, device)
+        if rank == 0:
+            print(json.dumps({"metric": "adjoint/forward time ratio", "value": round(tb / tf, 3), "unit": "ratio",
+                              "forward_s": tf, "backward_s": tb, "forward_MLUPS": n * 500 / tf / 1e6,
+                              "higher_is_better": False, "workload": args.workload}), flush=True)
+        return
     s, M0, solid = workload_solver(torch, device, args.workload)
-    s.set_moments(M0.to(device))
+    if WORKLOADS[args.workload][2] == "droplet":
+        s.set_moments(M0, s._phi0)
+    else:
+        s.set_moments(M0.to(device))
     del M0
     with ClockSampler(gpu_identifier(torch, device)) as clk:
         t = time_steps(torch, s, args.steps, args.warmup, barrier)
@@ -352,13 +390,16 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     lattice, storage, kind = WORKLOADS[args.workload]
     bpl = algorithmic_bytes(storage, mask=(kind == "channel"))
+    if kind == "droplet":
+        bpl += 4 * (1 + 1 + 3 + 3) + 4 * 3 * 2
     t_launch = t / args.steps
     achieved = bpl * n / t_launch / 1e9
     traffic = ncu_traffic(args.workload)
-    desc = WORKLOAD if args.workload == "channel256" else (
-        f"D3Q{lattice} {storage.upper()} storage, 512^3 periodic Taylor-Green U0=0.04 + random-phase perturbation "
-        "RMS 0.01 (seed 3), tau=0.55")
-    shape_xyz = [256, 256, 256] if kind == "channel" else [512, 512, 512]
+    desc = {"channel": WORKLOAD,
+            "droplet": "two-component D3Q19 FP32 128^3 static droplet R=20, W=4, sigma=0.03, D=0.1, tau=1",
+            "tg512": (f"D3Q{lattice} {storage.upper()} storage, 512^3 periodic Taylor-Green U0=0.04 + random-phase "
+                      "perturbation RMS 0.01 (seed 3), tau=0.55")}[kind]
+    shape_xyz = {"channel": [256, 256, 256], "droplet": [128, 128, 128], "tg512": [512, 512, 512]}[kind]
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 5), "higher_is_better": True,
