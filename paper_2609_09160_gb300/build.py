@@ -16,7 +16,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbf.so")
-SOURCES = ["api.cu", "kernels_d3q19.cu", "kernels_d3q27.cu", "static_step.cu"]
+SOURCES = ["api.cu", "static_step.cu", "kernels.cu"]
+# kernels.cu is compiled once per (lattice, storage) pair; each object holds that pair's kernels
+KERNEL_UNITS = [(q, s) for q in (19, 27) for s in range(4)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-O2", "-I", os.path.join(ROOT, "include")]
@@ -47,15 +49,29 @@ def up_to_date(tuning=()):
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    log = os.path.join(BUILD, os.path.basename(src) + ".log")
-    cmd = [nvcc()] + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
+def _units():
+    """(source, object name, defines) of every translation unit."""
+    units = []
+    for s in SOURCES:
+        src = os.path.join(CSRC, s)
+        if s == "kernels.cu":
+            for q, st in KERNEL_UNITS:
+                units.append((src, f"kernels_q{q}_s{st}", [f"-DLBF_TU_LATTICE={q}", f"-DLBF_TU_STORAGE={st}"]))
+        else:
+            units.append((src, os.path.splitext(s)[0], []))
+    return units
+
+
+def _compile(unit, extra):
+    src, name, defines = unit
+    obj = os.path.join(BUILD, name + ".o")
+    log = os.path.join(BUILD, name + ".log")
+    cmd = [nvcc()] + NVCC_FLAGS + defines + extra + ["-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     with open(log, "w") as f:
         f.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)
     if res.returncode != 0:
-        raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{res.stderr[-4000:]}")
+        raise RuntimeError(f"nvcc failed on {name}:\n{res.stderr[-4000:]}")
     return obj
 
 
@@ -67,9 +83,10 @@ def build(force=False, verbose_ptxas=False):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + tuning
-    srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
+    units = _units()
+    workers = max(1, min(len(units), os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        objs = list(ex.map(lambda u: _compile(u, extra), units))
     tmp = LIB + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
     res = subprocess.run(cmd, capture_output=True, text=True)

@@ -16,7 +16,8 @@
 //            lambda_A = (1 - omega) pi2 (stored off-diagonals doubled),
 //            dL/dF(y) += pi1 / (2 rho) + pi2 u / rho.
 // The kernel has the same z-marching shape as the forward one with the pull direction
-// reversed: staged values are w_q nu_q(x) and the gather reads y + c_q.
+// reversed: staged values are nu_q(x) (the weight w_q is applied in the gather sums) and the
+// gather reads y + c_q.
 #pragma once
 
 #include "stream_collide.cuh"
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS)
     Fn[0] = F[0];
     Fn[1] = F[1];
     Fn[2] = F[2];
-    // nu_q = (mu0 - tr Lam / 3) + c.g + c.Lam.c ; staged pre-multiplied by w_q
+    // nu_q = (mu0 - tr Lam / 3) + c.g + c.Lam.c
     PostColl<T> P;
     P.q0 = lp - (Lxx + Lyy + Lzz) * (T(1) / T(3));
     P.bx = gx_;
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS)
     static_for<Q>([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       if constexpr (q == REST) {
-        ps[q * ROWS * 32] = T(L::w(q)) * P.q0;
+        ps[q * ROWS * 32] = P.q0;
       } else if constexpr (q < L::opp(q)) {
         T fq, fo;
         pop_pair<L, q, T>(P, fq, fo);
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS)
         const bool walls = MASK && (any_m || any_0 || any_p);
         Accum<T> A = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         const T* base0 = nus + s_0 * PLANE + me;
-        A.a0 = base0[REST * ROWS * 32];
+        A.a0 = T(L::w(REST)) * base0[REST * ROWS * 32];
         static_for<Q>([&](auto qc) {
           constexpr int q = decltype(qc)::value;
           if constexpr (q != REST && q < L::opp(q)) {
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS)
                 if (msk[slot_o * ROWS * 32 + me + off_o]) go = base0[q * ROWS * 32];
               }
             }
-            accumulate_pair<cx, cy, cz, T>(A, gq, go);
+            accumulate_pair<cx, cy, cz, T>(A, gq, go, T(L::w(q)));
           }
         });
         const T third = T(1) / T(3);

@@ -172,8 +172,8 @@ struct lbf_ctx {
 
 namespace {
 
-KernelInfo forward_for(int Q, int storage, bool mask, bool two, bool tma) {
-  return Q == 19 ? forward_kernel_q19(storage, mask, two, tma) : forward_kernel_q27(storage, mask, two, tma);
+KernelInfo forward_for(int Q, int storage, bool mask, bool two, bool field, bool tma) {
+  return forward_kernel_for(Q, storage, mask, two, field, tma);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -201,9 +201,7 @@ bool tma_eligible(int storage, int nx) {
 
 // 4-D map over a state buffer: dims (x, y, z, field), box (box_x, rows, 1, 10)
 lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out);
-KernelInfo adjoint_for(int Q, int storage, bool mask) {
-  return Q == 19 ? adjoint_kernel_q19(storage, mask) : adjoint_kernel_q27(storage, mask);
-}
+KernelInfo adjoint_for(int Q, int storage, bool mask) { return adjoint_kernel_for(Q, storage, mask); }
 
 lbf_status prepare(const KernelInfo& k) {
   if (k.fn == nullptr) return LBF_OK;
@@ -356,6 +354,7 @@ FwdParams forward_params(const lbf_ctx* c, const void* src, void* dst, bool redu
   a.flags = c->flags;
   a.zchunk = c->zchunk;
   a.umax2 = 0.16f;
+  set_fp32_copies(a);
   return a;
 }
 
@@ -535,7 +534,7 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   set_scales(c, m0);
 
   c->tma = tma_eligible(c->storage, c->nx);
-  c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two, c->tma);
+  c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two, params->force_field != nullptr, c->tma);
   c->adj = adjoint_for(c->Q, c->storage, c->has_mask);
   if (c->fwd.fn == nullptr) {
     delete c;

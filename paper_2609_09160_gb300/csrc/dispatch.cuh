@@ -1,6 +1,6 @@
-// Launch-time dispatch from runtime parameters (lattice, storage dtype, mask, two-component) to the
-// kernel template instantiations. Each lattice's kernels are instantiated in their own
-// translation unit (kernels_d3q19.cu, kernels_d3q27.cu) so they compile in parallel.
+// Launch-time dispatch from runtime parameters (lattice, storage dtype, mask, force mode) to the
+// kernel template instantiations. The kernels of each (lattice, storage) pair are instantiated in
+// their own translation unit (kernels.cu compiled once per pair) so they compile in parallel.
 #pragma once
 
 #include "adjoint.cuh"
@@ -28,11 +28,11 @@ struct KernelInfo {
   int box_x;        // TMA box width in elements (0: the kernel loads without TMA)
 };
 
-template <class L, class S, bool MASK, bool TWO, bool TMA>
+template <class L, class S, bool MASK, bool TWO, bool FF, bool TMA>
 KernelInfo fwd_info() {
   constexpr int BY = fwd_rows(std::is_same<S, double>::value);
   KernelInfo k;
-  k.fn = reinterpret_cast<const void*>(&k_stream_collide<L, S, BY, MASK, TWO, TMA>);
+  k.fn = reinterpret_cast<const void*>(&k_stream_collide<L, S, BY, MASK, TWO, FF, TMA>);
   k.smem = fwd_smem_bytes<L, S, BY, MASK, TMA>();
   k.threads = FwdTile<BY>::THREADS;
   k.by = BY;
@@ -53,41 +53,55 @@ KernelInfo adj_info() {
   return k;
 }
 
+// forward kernel of lattice L and storage S for (mask, two-component, force field, TMA); fn ==
+// nullptr for combinations that are not built (two-component with a mask or a force field)
 template <class L, class S, bool TMA>
-KernelInfo forward_kernel_s(bool mask, bool two) {
-  if (mask) return fwd_info<L, S, true, false, TMA>();
-  return two ? fwd_info<L, S, false, true, TMA>() : fwd_info<L, S, false, false, TMA>();
+KernelInfo forward_kernel_s(bool mask, bool two, bool field) {
+  if (two) return (mask || field) ? KernelInfo{nullptr, 0, 0, 0, 0} : fwd_info<L, S, false, true, false, TMA>();
+  if (mask) return field ? fwd_info<L, S, true, false, true, TMA>() : fwd_info<L, S, true, false, false, TMA>();
+  return field ? fwd_info<L, S, false, false, true, TMA>() : fwd_info<L, S, false, false, false, TMA>();
 }
 
-// forward kernel for (storage, mask, two, tma) of lattice L; fn == nullptr if not built
-template <class L>
-KernelInfo forward_kernel(int storage, bool mask, bool two, bool tma) {
-  if (mask && two) return KernelInfo{nullptr, 0, 0, 0, 0};
+template <class L, class S>
+KernelInfo forward_kernel_ls(bool mask, bool two, bool field, bool tma) {
+  return tma ? forward_kernel_s<L, S, true>(mask, two, field) : forward_kernel_s<L, S, false>(mask, two, field);
+}
+
+// entry points implemented per (lattice, storage) translation unit
+#define LBF_DECLARE_TU(q, s)                                                             \
+  KernelInfo forward_kernel_q##q##_s##s(bool mask, bool two, bool field, bool tma); \
+  KernelInfo adjoint_kernel_q##q##_s##s(bool mask);
+LBF_DECLARE_TU(19, 0)
+LBF_DECLARE_TU(19, 1)
+LBF_DECLARE_TU(19, 2)
+LBF_DECLARE_TU(19, 3)
+LBF_DECLARE_TU(27, 0)
+LBF_DECLARE_TU(27, 1)
+LBF_DECLARE_TU(27, 2)
+LBF_DECLARE_TU(27, 3)
+#undef LBF_DECLARE_TU
+
+inline KernelInfo forward_kernel_for(int lattice, int storage, bool mask, bool two, bool field, bool tma) {
+  const bool q19 = lattice == 19;
   switch (storage) {
-    case ST_F64: return tma ? forward_kernel_s<L, double, true>(mask, two) : forward_kernel_s<L, double, false>(mask, two);
-    case ST_F32: return tma ? forward_kernel_s<L, float, true>(mask, two) : forward_kernel_s<L, float, false>(mask, two);
-    case ST_F16: return tma ? forward_kernel_s<L, __half, true>(mask, two) : forward_kernel_s<L, __half, false>(mask, two);
-    case ST_BF16:
-      return tma ? forward_kernel_s<L, __nv_bfloat16, true>(mask, two) : forward_kernel_s<L, __nv_bfloat16, false>(mask, two);
+    case ST_F64: return q19 ? forward_kernel_q19_s0(mask, two, field, tma) : forward_kernel_q27_s0(mask, two, field, tma);
+    case ST_F32: return q19 ? forward_kernel_q19_s1(mask, two, field, tma) : forward_kernel_q27_s1(mask, two, field, tma);
+    case ST_F16: return q19 ? forward_kernel_q19_s2(mask, two, field, tma) : forward_kernel_q27_s2(mask, two, field, tma);
+    case ST_BF16: return q19 ? forward_kernel_q19_s3(mask, two, field, tma) : forward_kernel_q27_s3(mask, two, field, tma);
   }
   return KernelInfo{nullptr, 0, 0, 0, 0};
 }
 
-template <class L>
-KernelInfo adjoint_kernel(int storage, bool mask) {
+// adjoint kernel (FP64 and FP32 storage only; fn == nullptr otherwise)
+inline KernelInfo adjoint_kernel_for(int lattice, int storage, bool mask) {
+  const bool q19 = lattice == 19;
   switch (storage) {
-    case ST_F64:
-      return mask ? adj_info<L, double, true>() : adj_info<L, double, false>();
-    case ST_F32:
-      return mask ? adj_info<L, float, true>() : adj_info<L, float, false>();
+    case ST_F64: return q19 ? adjoint_kernel_q19_s0(mask) : adjoint_kernel_q27_s0(mask);
+    case ST_F32: return q19 ? adjoint_kernel_q19_s1(mask) : adjoint_kernel_q27_s1(mask);
+    case ST_F16: return q19 ? adjoint_kernel_q19_s2(mask) : adjoint_kernel_q27_s2(mask);
+    case ST_BF16: return q19 ? adjoint_kernel_q19_s3(mask) : adjoint_kernel_q27_s3(mask);
   }
   return KernelInfo{nullptr, 0, 0, 0, 0};
 }
-
-// entry points implemented per lattice (one translation unit each)
-KernelInfo forward_kernel_q19(int storage, bool mask, bool two, bool tma);
-KernelInfo forward_kernel_q27(int storage, bool mask, bool two, bool tma);
-KernelInfo adjoint_kernel_q19(int storage, bool mask);
-KernelInfo adjoint_kernel_q27(int storage, bool mask);
 
 }  // namespace lbf

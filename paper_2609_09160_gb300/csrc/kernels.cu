@@ -1,0 +1,48 @@
+// Kernel instantiations of one (lattice, storage) pair: the fused step in every force / mask / TMA
+// variant and, for FP64 and FP32 storage, its adjoint. The build compiles this file once per pair
+// with LBF_TU_LATTICE (19 or 27) and LBF_TU_STORAGE (0 FP64, 1 FP32, 2 FP16, 3 BF16) defined.
+#include "dispatch.cuh"
+
+#if !defined(LBF_TU_LATTICE) || !defined(LBF_TU_STORAGE)
+#error "compile kernels.cu with -DLBF_TU_LATTICE=19|27 -DLBF_TU_STORAGE=0..3"
+#endif
+
+namespace lbf {
+namespace {
+#if LBF_TU_LATTICE == 19
+using TuL = D3Q19;
+#elif LBF_TU_LATTICE == 27
+using TuL = D3Q27;
+#else
+#error "LBF_TU_LATTICE must be 19 or 27"
+#endif
+#if LBF_TU_STORAGE == 0
+using TuS = double;
+#elif LBF_TU_STORAGE == 1
+using TuS = float;
+#elif LBF_TU_STORAGE == 2
+using TuS = __half;
+#elif LBF_TU_STORAGE == 3
+using TuS = __nv_bfloat16;
+#else
+#error "LBF_TU_STORAGE must be 0..3"
+#endif
+}  // namespace
+
+#define LBF_CAT2(a, b, c, d) a##b##c##d
+#define LBF_CAT(a, b, c, d) LBF_CAT2(a, b, c, d)
+
+KernelInfo LBF_CAT(forward_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask, bool two, bool field, bool tma) {
+  return forward_kernel_ls<TuL, TuS>(mask, two, field, tma);
+}
+
+KernelInfo LBF_CAT(adjoint_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask) {
+#if LBF_TU_STORAGE <= 1
+  return mask ? adj_info<TuL, TuS, true>() : adj_info<TuL, TuS, false>();
+#else
+  (void)mask;
+  return KernelInfo{nullptr, 0, 0, 0, 0};
+#endif
+}
+
+}  // namespace lbf

@@ -106,8 +106,8 @@ extern "C" lbf_status lbf_step_static(const lbf_params* params, const void* src,
   const size_t es = params->storage == LBF_F64 ? 8 : 4;
   PFN_cuTensorMapEncodeTiled_v12000 enc = static_encoder();
   const bool tma = enc != nullptr && (size_t(nx) * es) % 16 == 0 && std::getenv("LBF_NO_TMA") == nullptr;
-  const KernelInfo k = params->lattice == 19 ? forward_kernel_q19(params->storage, mask_device != nullptr, false, tma)
-                                             : forward_kernel_q27(params->storage, mask_device != nullptr, false, tma);
+  const KernelInfo k = forward_kernel_for(params->lattice, params->storage, mask_device != nullptr, false,
+                                          params->force_field != nullptr, tma);
   if (k.fn == nullptr) return fail(LBF_ENOTSUP, "no kernel for this combination");
 
   // grid: 30 x by output columns per CTA, z-chunks of about 32 planes, at most kStaticMaxBlocks CTAs
@@ -148,6 +148,7 @@ extern "C" lbf_status lbf_step_static(const lbf_params* params, const void* src,
   a.flags = flags;
   a.zchunk = zc;
   a.umax2 = 0.16f;
+  set_fp32_copies(a);
 
   CUtensorMap tm;
   std::memset(&tm, 0, sizeof(tm));

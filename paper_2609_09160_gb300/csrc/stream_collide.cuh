@@ -57,7 +57,27 @@ struct FwdParams {
   unsigned* flags;          // bit 0: non-finite or |u|^2 > umax2 seen
   int zchunk;
   float umax2;
+  // FP32 copies of the double scalars above (set_fp32_copies), read by the FP32-compute kernels
+  float force_f[3], omega_f, rho_l_f, drho_f, nu_l_f, dnu_f;
 };
+
+inline void set_fp32_copies(FwdParams& a) {
+  for (int k = 0; k < 3; ++k) a.force_f[k] = float(a.force[k]);
+  a.omega_f = float(a.omega);
+  a.rho_l_f = float(a.rho_l);
+  a.drho_f = float(a.rho_h - a.rho_l);
+  a.nu_l_f = float(a.nu_l);
+  a.dnu_f = float(a.nu_h - a.nu_l);
+}
+
+// a kernel scalar in the compute type: the FP64 value for FP64 compute, else its FP32 copy
+template <class T>
+__device__ __forceinline__ T pick(double d, float f) {
+  if constexpr (std::is_same<T, double>::value)
+    return d;
+  else
+    return f;
+}
 
 template <class S, class T>
 __device__ __forceinline__ T ld_field(const S* base, long long idx, float dec) {
@@ -111,7 +131,8 @@ __device__ __forceinline__ PostColl<T> post_collision(T p, T ux, T uy, T uz, T n
   return r;
 }
 
-// f_q and f_opp(q) of one site: w_q (s +/- d) with s = q0 + c.e.c and d = c.b
+// f_q / w_q and f_opp(q) / w_q of one site: s +/- d with s = q0 + c.e.c and d = c.b. The weight
+// w_q (equal for q and opp(q)) is applied where the pulled populations are summed.
 template <class L, int q, class T>
 __device__ __forceinline__ void pop_pair(const PostColl<T>& P, T& fq, T& fo) {
   constexpr int cx = L::cx(q), cy = L::cy(q), cz = L::cz(q);
@@ -133,9 +154,8 @@ __device__ __forceinline__ void pop_pair(const PostColl<T>& P, T& fq, T& fo) {
   } else {
     d = (cz > 0) ? P.bz : -P.bz;
   }
-  constexpr T w = T(L::w(q));
-  fq = w * (s + d);
-  fo = w * (s - d);
+  fq = s + d;
+  fo = s - d;
 }
 
 // new raw moments accumulated from pulled populations, pairwise
@@ -144,19 +164,31 @@ struct Accum {
   T a0, jx, jy, jz, rxx, ryy, rzz, rxy, rxz, ryz;
 };
 
+// acc + C w v for a compile-time C in {-1, 0, 1}
+template <int C, class T>
+__device__ __forceinline__ T sfma(T acc, T w, T v) {
+  if constexpr (C > 0)
+    return fma(w, v, acc);
+  else if constexpr (C < 0)
+    return fma(-w, v, acc);
+  else
+    return acc;
+}
+
+// adds the pair (f_q, f_opp(q)) = w (gq, go) of direction c = (cx, cy, cz) with weight w
 template <int cx, int cy, int cz, class T>
-__device__ __forceinline__ void accumulate_pair(Accum<T>& A, T fq, T fo) {
-  const T s = fq + fo, d = fq - fo;
-  A.a0 += s;
-  A.jx = sadd<cx>(A.jx, d);
-  A.jy = sadd<cy>(A.jy, d);
-  A.jz = sadd<cz>(A.jz, d);
-  A.rxx = sadd<cx * cx>(A.rxx, s);
-  A.ryy = sadd<cy * cy>(A.ryy, s);
-  A.rzz = sadd<cz * cz>(A.rzz, s);
-  A.rxy = sadd<cx * cy>(A.rxy, s);
-  A.rxz = sadd<cx * cz>(A.rxz, s);
-  A.ryz = sadd<cy * cz>(A.ryz, s);
+__device__ __forceinline__ void accumulate_pair(Accum<T>& A, T gq, T go, T w) {
+  const T s = gq + go, d = gq - go;
+  A.a0 = fma(w, s, A.a0);
+  A.jx = sfma<cx>(A.jx, w, d);
+  A.jy = sfma<cy>(A.jy, w, d);
+  A.jz = sfma<cz>(A.jz, w, d);
+  A.rxx = sfma<cx * cx>(A.rxx, w, s);
+  A.ryy = sfma<cy * cy>(A.ryy, w, s);
+  A.rzz = sfma<cz * cz>(A.rzz, w, s);
+  A.rxy = sfma<cx * cy>(A.rxy, w, s);
+  A.rxz = sfma<cx * cz>(A.rxz, w, s);
+  A.ryz = sfma<cy * cz>(A.ryz, w, s);
 }
 
 template <int BY>
@@ -260,7 +292,7 @@ struct SiteExtra {
 
 constexpr uint32_t kWaitPolls = 1u << 20;  // bound of every mbarrier wait
 
-template <class L, class S, int BY, bool MASK, bool TWO, bool TMA>
+template <class L, class S, int BY, bool MASK, bool TWO, bool FF, bool TMA>
 __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>::value ? 1 : LBF_FWD_MINB)
     k_stream_collide(const FwdParams a, const __grid_constant__ CUtensorMap tmap) {
   using T = typename ComputeOf<S>::type;
@@ -277,6 +309,8 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   constexpr int STAGE_STRIDE = int(raw_stage_bytes<S, ROWS>() / sizeof(S));   // padded stage
   constexpr size_t RAW_BYTES = TMA ? 128 + size_t(kRawStages) * raw_stage_bytes<S, ROWS>() : 0;
   constexpr int G0 = D::gsize(0) * SITES, G1 = D::gsize(1) * SITES, G2 = D::gsize(2) * SITES;
+  constexpr int GS2 = D::gsize(2);  // three-slot offsets: ring g2 = slot * G2, solid flags g2 / GS2
+  constexpr bool SITEF = TWO || FF;  // per-site force (else the uniform force of the parameters)
   static_assert(fwd_smem_bytes<L, S, BY, MASK, TMA>() >= 6 * 512 * sizeof(double), "smem too small for the final tree");
   static_assert(FwdTile<BY>::THREADS <= 512, "final tree assumes <= 512 threads");
   static_assert(kRawStages == 2, "plane parities below assume two raw stages");
@@ -312,9 +346,9 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   const int z0 = blockIdx.z * a.zchunk;
   const int z1 = min(a.nz, z0 + a.zchunk);
   const int me = row * 32 + lane;
-  const T one_m_omega = T(1) - T(a.omega);
-  const T Fu0 = T(a.force[0]), Fu1 = T(a.force[1]), Fu2 = T(a.force[2]);
-  const bool has_field = ffield != nullptr;
+  const T one_m_omega = T(1) - pick<T>(a.omega, a.omega_f);
+  const T Fu0 = pick<T>(a.force[0], a.force_f[0]), Fu1 = pick<T>(a.force[1], a.force_f[1]),
+          Fu2 = pick<T>(a.force[2], a.force_f[2]);
   // planes of the chunk window are numbered r = p - (z0 - 1) >= 0: raw stage and the two-slot ring
   // groups use r & 1, the three-slot group and the solid flags rotate through three slots
   const int pbase = z0 - 1;
@@ -361,16 +395,11 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
         e.Fn[1] = __ldg(Fn + N + col);
         e.Fn[2] = __ldg(Fn + 2 * N + col);
       }
-    } else {
-      e.F[0] = Fu0;
-      e.F[1] = Fu1;
-      e.F[2] = Fu2;
-      if (has_field) {
-        const T* fb = ffield + zoff;
-        e.F[0] += __ldg(fb + col);
-        e.F[1] += __ldg(fb + N + col);
-        e.F[2] += __ldg(fb + 2 * N + col);
-      }
+    } else if constexpr (FF) {
+      const T* fb = ffield + zoff;
+      e.F[0] = Fu0 + __ldg(fb + col);
+      e.F[1] = Fu1 + __ldg(fb + N + col);
+      e.F[2] = Fu2 + __ldg(fb + 2 * N + col);
     }
     if constexpr (MASK) e.solid = __ldg(a.mask + zoff + col) != 0;
     else e.solid = false;
@@ -412,34 +441,35 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   // three-slot ring offsets (elements of the c_z = +1 group, bytes of the solid flags) of the
   // planes z-1, z, z+1; they rotate by one slot per plane
   int g2m = 0, g20 = G2, g2p = 2 * G2;
-  int mkm = 0, mk0 = SITES, mkp = 2 * SITES;
 
   // -- staging: post-collision populations of plane p into the ring ----------------------------
-  // par: (p - pbase) & 1 (compile time); g2, mk: the three-slot offsets of plane p
-  auto stage = [&](auto par_c, int p, int g2, int mk, const SiteExtra<T, TWO>& e) -> bool {
+  // par: (p - pbase) & 1 (compile time); g2: the three-slot offset of plane p
+  auto stage = [&](auto par_c, int p, int g2, const SiteExtra<T, TWO>& e) -> bool {
     constexpr int par = decltype(par_c)::value;
     T m[10];
     read_raw(p, par, m);
     T inv2rho = T(0.5), omm = one_m_omega;
     if constexpr (TWO) {
-      const T rho = T(a.rho_l) + e.phi_o * T(a.rho_h - a.rho_l);
-      const T nu = T(a.nu_l) + e.phi_o * T(a.nu_h - a.nu_l);
+      const T rho_l = pick<T>(a.rho_l, a.rho_l_f), drho = pick<T>(a.rho_h - a.rho_l, a.drho_f);
+      const T rho = rho_l + e.phi_o * drho;
+      const T nu = pick<T>(a.nu_l, a.nu_l_f) + e.phi_o * pick<T>(a.nu_h - a.nu_l, a.dnu_f);
       inv2rho = T(0.5) / rho;
       omm = T(1) - T(1) / (T(3) * nu + T(0.5));
       if (outcol) {
         phi_next = e.phi_n;
-        i2r_next = T(0.5) / (T(a.rho_l) + e.phi_n * T(a.rho_h - a.rho_l));
+        i2r_next = T(0.5) / (rho_l + e.phi_n * drho);
         Fnext[0] = e.Fn[0];
         Fnext[1] = e.Fn[1];
         Fnext[2] = e.Fn[2];
       }
-    } else {
+    } else if constexpr (FF) {
       Fnext[0] = e.F[0];
       Fnext[1] = e.F[1];
       Fnext[2] = e.F[2];
     }
-    const PostColl<T> P = post_collision<T>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9], e.F[0],
-                                            e.F[1], e.F[2], inv2rho, omm);
+    const T Fs0 = SITEF ? e.F[0] : Fu0, Fs1 = SITEF ? e.F[1] : Fu1, Fs2 = SITEF ? e.F[2] : Fu2;
+    const PostColl<T> P =
+        post_collision<T>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9], Fs0, Fs1, Fs2, inv2rho, omm);
     T* w0 = ring + R::base(0) + par * G0 + me;
     T* w1 = ring + R::base(1) + par * G1 + me;
     T* w2 = ring + R::base(2) + g2 + me;
@@ -458,7 +488,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     static_for<Q>([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       if constexpr (q == QREST) {
-        rest_new = T(L::w(q)) * P.q0;
+        rest_new = P.q0;
       } else if constexpr (q < L::opp(q)) {
         T fq, fo;
         pop_pair<L, q, T>(P, fq, fo);
@@ -466,7 +496,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
         put(std::integral_constant<int, L::opp(q)>{}, fo);
       }
     });
-    if constexpr (MASK) msk[mk + me] = e.solid ? 1 : 0;
+    if constexpr (MASK) msk[g2 / GS2 + me] = e.solid ? 1 : 0;
     sol_new = e.solid;
     return e.solid;
   };
@@ -503,7 +533,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     wait_plane(z0 - 1);
     waited = z0 - 1;
   }
-  bool any_m = stage(std::integral_constant<int, 0>{}, z0 - 1, g2m, mkm, ex);
+  bool any_m = stage(std::integral_constant<int, 0>{}, z0 - 1, g2m, ex);
   up_m1 = up_new;
   sol_m1 = sol_new;
   load_extra(z0, ex);
@@ -516,7 +546,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     wait_plane(z0);
     waited = z0;
   }
-  bool any_0 = stage(std::integral_constant<int, 1>{}, z0, g20, mk0, ex);
+  bool any_0 = stage(std::integral_constant<int, 1>{}, z0, g20, ex);
   up_0 = up_new;
   dn_0 = dn_new;
   rest_0 = rest_new;
@@ -542,8 +572,8 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
       wait_plane(z + 1);
       waited = z + 1;
     }
-    bool any_p = stage(std::integral_constant<int, PAR>{}, z + 1, g2p, mkp, ex);
-    if (z + 2 <= z1) load_extra(z + 2, ex);  // in flight during the outputs of plane z
+    bool any_p = stage(std::integral_constant<int, PAR>{}, z + 1, g2p, ex);
+    load_extra(z + 2, ex);  // in flight during the outputs of plane z (z + 2 <= nz + 1 wraps)
     if constexpr (MASK)
       any_p = __syncthreads_or(any_p);
     else
@@ -560,10 +590,10 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
         constexpr bool W = decltype(walls_c)::value;
         const T* O0 = ring + R::base(0) + (PAR ^ 1) * G0 + me;  // own site, plane z
         const T* O2 = ring + R::base(2) + g20 + me;
-        const uint8_t* MM = msk + mkm + me;
-        const uint8_t* M0 = msk + mk0 + me;
-        const uint8_t* MP = msk + mkp + me;
-        Accum<T> A = {rest_0, T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        const uint8_t* MM = msk + g2m / GS2 + me;
+        const uint8_t* M0 = msk + g20 / GS2 + me;
+        const uint8_t* MP = msk + g2p / GS2 + me;
+        Accum<T> A = {T(L::w(QREST)) * rest_0, T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         auto pulled = [&](auto qc) -> T {
           constexpr int q = decltype(qc)::value;
           constexpr int cx = L::cx(q), cy = L::cy(q), cz = L::cz(q);
@@ -585,7 +615,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
           if constexpr (q != QREST && q < L::opp(q) && q != QUP && q != QDN) {
             const T fq = pulled(qc);
             const T fo = pulled(std::integral_constant<int, L::opp(q)>{});
-            accumulate_pair<L::cx(q), L::cy(q), L::cz(q), T>(A, fq, fo);
+            accumulate_pair<L::cx(q), L::cy(q), L::cz(q), T>(A, fq, fo, T(L::w(q)));
           }
         });
         // axial pair: (0,0,+1) comes from the plane below, (0,0,-1) from the plane above
@@ -594,7 +624,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
           if (sol_m1) fup = dn_0;
           if (sol_new) fdn = up_0;
         }
-        accumulate_pair<0, 0, 1, T>(A, fup, fdn);
+        accumulate_pair<0, 0, 1, T>(A, fup, fdn, T(L::w(QUP)));
         return A;
       };
       Accum<T> A;
@@ -608,7 +638,8 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
       }
       // Eq. (corr): u = a1 + F/(2 rho), a2 = (sum c c f - cs2 a0 delta) + (u F + F u)/(2 rho)
       const T i2r = i2r_own;
-      const T hx = Fown[0] * i2r, hy = Fown[1] * i2r, hz = Fown[2] * i2r;
+      const T hx = (SITEF ? Fown[0] : Fu0) * i2r, hy = (SITEF ? Fown[1] : Fu1) * i2r,
+              hz = (SITEF ? Fown[2] : Fu2) * i2r;
       const T ux = A.jx + hx, uy = A.jy + hy, uz = A.jz + hz;
       const T a0c = A.a0 * (T(1) / T(3));
       const T nxx = (A.rxx - a0c) + T(2) * ux * hx - ux * ux;
@@ -635,7 +666,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
         red[1] += ux;
         red[2] += uy;
         red[3] += uz;
-        red[4] += phi_own;
+        if constexpr (TWO) red[4] += phi_own;
         red[5] += uu;
       }
     }
@@ -657,10 +688,6 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     g2m = g20;
     g20 = g2p;
     g2p = g2t;
-    const int mkt = mkm;
-    mkm = mk0;
-    mk0 = mkp;
-    mkp = mkt;
     __syncthreads();
   };
 
