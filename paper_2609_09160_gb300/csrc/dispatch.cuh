@@ -10,14 +10,8 @@ namespace lbf {
 
 enum StorageId { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
-// output rows per CTA of the forward kernel (FP32 compute / FP64 compute) and of the adjoint
-#ifndef LBF_FWD_ROWS
-#define LBF_FWD_ROWS 8
-#endif
-#ifndef LBF_FWD_ROWS_F64
-#define LBF_FWD_ROWS_F64 4
-#endif
-constexpr int fwd_rows(bool fp64) { return fp64 ? LBF_FWD_ROWS_F64 : LBF_FWD_ROWS; }
+// output rows per CTA of the adjoint kernel (FP32 compute / FP64 compute); the forward kernel's
+// are fwd_rows() of stream_collide.cuh
 constexpr int adj_rows(bool fp64) { return fp64 ? 4 : 8; }
 
 struct KernelInfo {
@@ -30,7 +24,7 @@ struct KernelInfo {
 
 template <class L, class S, bool MASK, bool TWO, bool FF, bool TMA>
 KernelInfo fwd_info() {
-  constexpr int BY = fwd_rows(std::is_same<S, double>::value);
+  constexpr int BY = fwd_rows(L::Q, std::is_same<S, double>::value);
   KernelInfo k;
   k.fn = reinterpret_cast<const void*>(&k_stream_collide<L, S, BY, MASK, TWO, FF, TMA>);
   k.smem = fwd_smem_bytes<L, S, BY, MASK, TMA>();

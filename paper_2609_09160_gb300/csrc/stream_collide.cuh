@@ -284,16 +284,34 @@ struct SiteExtra {
   bool solid;
 };
 
-// minimum resident CTAs per SM asked of the register allocator (320-thread CTAs: 3 -> <= 64
-// registers per thread)
-#ifndef LBF_FWD_MINB
-#define LBF_FWD_MINB 3
+// output rows per CTA (FP32 compute per lattice, FP64 compute) and the minimum resident CTAs per
+// SM asked of the register allocator. D3Q19 FP32: 8 rows, 3 CTAs of 320 threads (<= 64
+// registers), limited by shared memory to 3; D3Q27: its larger ring fits 2 CTAs, so 2 (<= 96
+// registers).
+#ifndef LBF_FWD_ROWS_Q19
+#define LBF_FWD_ROWS_Q19 8
 #endif
+#ifndef LBF_FWD_ROWS_Q27
+#define LBF_FWD_ROWS_Q27 8
+#endif
+#ifndef LBF_FWD_ROWS_F64
+#define LBF_FWD_ROWS_F64 4
+#endif
+#ifndef LBF_FWD_MINB_Q19
+#define LBF_FWD_MINB_Q19 3
+#endif
+#ifndef LBF_FWD_MINB_Q27
+#define LBF_FWD_MINB_Q27 2
+#endif
+constexpr int fwd_rows(int Q, bool fp64) {
+  return fp64 ? LBF_FWD_ROWS_F64 : (Q == 19 ? LBF_FWD_ROWS_Q19 : LBF_FWD_ROWS_Q27);
+}
+constexpr int fwd_minb(int Q, bool fp64) { return fp64 ? 1 : (Q == 19 ? LBF_FWD_MINB_Q19 : LBF_FWD_MINB_Q27); }
 
 constexpr uint32_t kWaitPolls = 1u << 20;  // bound of every mbarrier wait
 
 template <class L, class S, int BY, bool MASK, bool TWO, bool FF, bool TMA>
-__global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>::value ? 1 : LBF_FWD_MINB)
+__global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, std::is_same<S, double>::value))
     k_stream_collide(const FwdParams a, const __grid_constant__ CUtensorMap tmap) {
   using T = typename ComputeOf<S>::type;
   using D = Dirs<L>;
@@ -354,6 +372,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   const int pbase = z0 - 1;
   const S* raw_me = rawst + row * BX + lane + xoff;  // this thread's site in stage 0
 
+  int issued = pbase - 1;  // last plane whose TMA load was issued (elected thread)
   auto issue = [&](int p) {  // elected thread only
     if (p > z1 || abort_flag) return;
     const int s = (p - pbase) & 1;
@@ -363,9 +382,11 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
       abort_flag = 1;
       return;
     }
-    fence_proxy_async_smem();
+    // no proxy fence: the stage is only read through the generic proxy, and every read of it
+    // completed before the barrier that precedes this call
     mbar_arrive_expect_tx(&bars[s], uint32_t(STAGE_ELEMS * sizeof(S)));
     tma_load_4d(dstp, &tmap, &bars[s], xa, int(blockIdx.y) * BY - 1, wrap(p, a.nz), 0);
+    issued = p;
   };
   auto wait_plane = [&](int p) {
     if (abort_flag) return;
@@ -525,13 +546,11 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
       for (int p = pbase; p < pbase + kRawStages; ++p) issue(p);
     }
   }
-  int waited = pbase - 1;  // last plane whose TMA was waited for
 
   // prologue: stage planes z0-1 (r = 0) and z0 (r = 1)
   load_extra(z0 - 1, ex);
   if constexpr (TMA) {
     wait_plane(z0 - 1);
-    waited = z0 - 1;
   }
   bool any_m = stage(std::integral_constant<int, 0>{}, z0 - 1, g2m, ex);
   up_m1 = up_new;
@@ -544,9 +563,11 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   if constexpr (TMA) {
     if (me == 0) issue(z0 - 1 + kRawStages);
     wait_plane(z0);
-    waited = z0;
   }
   bool any_0 = stage(std::integral_constant<int, 1>{}, z0, g20, ex);
+  if constexpr (TMA) {
+    if (!out_row) wait_plane(z0 + 1);  // staged by the first iteration (z0 + 1 <= z1)
+  }
   up_0 = up_new;
   dn_0 = dn_new;
   rest_0 = rest_new;
@@ -568,10 +589,8 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   // one plane: stage z+1, outputs of z. PAR = (z - z0) & 1 at compile time
   auto iteration = [&](auto par_c, int z) {
     constexpr int PAR = decltype(par_c)::value;
-    if constexpr (TMA) {
-      wait_plane(z + 1);
-      waited = z + 1;
-    }
+    // plane z+1 has landed: the y-halo warps waited for it before the barrier that ended the
+    // previous iteration (or the prologue), and that barrier orders the observation for everyone
     bool any_p = stage(std::integral_constant<int, PAR>{}, z + 1, g2p, ex);
     load_extra(z + 2, ex);  // in flight during the outputs of plane z (z + 2 <= nz + 1 wraps)
     if constexpr (MASK)
@@ -688,6 +707,9 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
     g2m = g20;
     g20 = g2p;
     g2p = g2t;
+    if constexpr (TMA) {
+      if (!out_row && z + 2 <= z1) wait_plane(z + 2);  // staged by the next iteration
+    }
     __syncthreads();
   };
 
@@ -699,8 +721,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, std::is_same<S, double>:
   if constexpr (TMA) {
     // after an aborted wait, let the copies still in flight land before the CTA exits (bounded)
     if (abort_flag && me == 0) {
-      const int last_issued = min(z1, waited + kRawStages);
-      for (int p = waited; p <= last_issued; ++p) {
+      for (int p = max(pbase, issued - kRawStages + 1); p <= issued; ++p) {
         const int s = (p - pbase) & 1;
         mbar_wait_bounded(&bars[s], uint32_t((p - pbase) >> 1) & 1u, kWaitPolls);
       }
