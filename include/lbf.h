@@ -18,6 +18,10 @@
  *  - Internal state ("state buffer"): the same 10 fields in the storage dtype, with the tensor
  *    stored as N = A - u u and, for 16-bit storage, every group multiplied by a power of two.
  *    Callers treat it as opaque bytes of size lbf_state_bytes().
+ *  - 16-bit storage: a time step rounds the values it stores stochastically (unbiased), with
+ *    random bits from a counter-based generator keyed by the site and the context's count of
+ *    steps taken, so results are bitwise reproducible for the same sequence of calls. Loading a
+ *    state (lbf_set_moments) rounds to nearest.
  *  - Every call is ordered on the context's CUDA stream (lbf_params.stream) and returns without
  *    waiting for the GPU, except lbf_reduce and lbf_synchronize, which wait for the stream.
  *  - The library allocates no device memory: the caller provides one workspace of

@@ -83,23 +83,35 @@ __device__ __forceinline__ void static_for(F&& f) {
 template <class S>
 struct Codec;
 
+// store: round to nearest (loading a state). store_sr: unbiased stochastic rounding with the
+// random word r, used by the time step. Round-to-nearest of a 16-bit state discards every update
+// smaller than half a unit in the last place: on large lattices, where the flow changes by less
+// than 2^-12 of its value per step, the state then freezes and its error grows with time.
+// Adding uniform random bits below the kept significand and truncating rounds up with
+// probability equal to the discarded fraction, so the expected stored value is exact.
 template <>
 struct Codec<double> {
   static constexpr bool scaled = false;
   __device__ __forceinline__ static double load(const double* p) { return __ldg(p); }
   __device__ __forceinline__ static void store(double* p, double v) { *p = v; }
+  __device__ __forceinline__ static void store_sr(double* p, double v, uint32_t) { *p = v; }
 };
 template <>
 struct Codec<float> {
   static constexpr bool scaled = false;
   __device__ __forceinline__ static float load(const float* p) { return __ldg(p); }
   __device__ __forceinline__ static void store(float* p, float v) { *p = v; }
+  __device__ __forceinline__ static void store_sr(float* p, float v, uint32_t) { *p = v; }
 };
 template <>
 struct Codec<__half> {
   static constexpr bool scaled = true;
   __device__ __forceinline__ static float load(const __half* p) { return __half2float(__ldg(p)); }
   __device__ __forceinline__ static void store(__half* p, float v) { *p = __float2half_rn(v); }
+  // FP16 keeps 10 of FP32's 23 significand bits: 13 random bits, then round toward zero
+  __device__ __forceinline__ static void store_sr(__half* p, float v, uint32_t r) {
+    *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (r >> 19)));
+  }
 };
 template <>
 struct Codec<__nv_bfloat16> {
@@ -108,7 +120,25 @@ struct Codec<__nv_bfloat16> {
     return __bfloat162float(__ldg(p));
   }
   __device__ __forceinline__ static void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+  // BF16 is the upper half of FP32: 16 random bits, then truncation
+  __device__ __forceinline__ static void store_sr(__nv_bfloat16* p, float v, uint32_t r) {
+    *p = __ushort_as_bfloat16(static_cast<unsigned short>((__float_as_uint(v) + (r >> 16)) >> 16));
+  }
 };
+
+// Counter-based random words for stochastic rounding. fmix32 is the 32-bit finaliser of
+// MurmurHash3 (A. Appleby): a bijective mixer that turns a counter into a uniformly distributed
+// word. Successive words for one site come from the linear congruential step of the PCG family
+// (M. E. O'Neill: multiplier 747796405, increment 2891336453); the high bits are used.
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint32_t lcg_next(uint32_t s) { return s * 747796405u + 2891336453u; }
 
 // per-group scale factors passed by value to every kernel
 struct Scales {
