@@ -90,7 +90,7 @@ lbf_status check_params(const lbf_params* p) {
 
 int grid_x(int nx) { return (nx + FwdTile<8>::XOUT - 1) / FwdTile<8>::XOUT; }
 int grid_y(int ny, int by) { return (ny + by - 1) / by; }
-int fwd_by(int Q, int storage) { return fwd_rows(Q, storage == LBF_F64); }
+int fwd_by(int Q, int storage) { return fwd_rows(Q, int(storage_bytes(storage))); }
 int min_zchunk(int nz) { return std::min(8, nz); }
 
 bool make_layout(const lbf_params* p, Layout* L) {
@@ -288,13 +288,14 @@ PhaseParams phase_params(const lbf_ctx* c) {
   pp.kappa = 1.5 * c->prm.sigma * c->prm.width;
   for (int a = 0; a < 3; ++a) pp.body[a] = c->prm.force[a];
   pp.sc = c->sc;
+  pp.zchunk = c->zchunk;
   return pp;
 }
 
-dim3 phase_block() { return dim3(32, 4, 2); }
+// phase-field kernels: the fused step's x-y tiles (30 x kPhaseRows outputs), z-chunks of zchunk
+dim3 phase_block() { return dim3(32, kPhaseRows + 2, 1); }
 dim3 phase_grid(const lbf_ctx* c) {
-  const dim3 b = phase_block();
-  return dim3((c->nx + b.x - 1) / b.x, (c->ny + b.y - 1) / b.y, (c->nz + b.z - 1) / b.z);
+  return dim3((c->nx + 29) / 30, (c->ny + kPhaseRows - 1) / kPhaseRows, (c->nz + c->zchunk - 1) / c->zchunk);
 }
 
 template <class T>

@@ -141,107 +141,189 @@ __global__ void k_reduce_final(const double* __restrict__ partials, long long nb
 //   div V = 3 sum_i w_i c_i . V(x + c_i)
 // Allen-Cahn FTCS in flux form: phi' = phi - div(phi u) + D lap phi - lambda div(G),
 // G = phi (1 - phi) n, n = grad phi / max(|grad phi|, 1e-12), lambda = 4 D / W.
+//
+// The D3Q27 weights are products of one-dimensional weights, w_i = a(c_x) a(c_y) a(c_z) with
+// a(0) = 2/3 and a(+-1) = 1/6, so every stencil above separates into three-point filters along
+// the axes: the smoothing A f = a(0) f(0) + a(1) (f(-1) + f(+1)) and the difference
+// D f = (f(+1) - f(-1)) / 6, e.g. sum_i w_i c_i,x psi(x + c_i) = D_x A_y A_z psi and
+// sum_i w_i psi(x + c_i) = A_x A_y A_z psi. The Laplacian is assembled from second differences
+// only, with L = A - I = (1/6) [1, -2, 1]:
+//   sum_i w_i (psi(x + c_i) - psi(x)) = L_x A_y psi + L_y psi + A_x A_y L_z psi,
+// so that, as in the flux form, every term vanishes exactly on a constant field: the rounded
+// weights 2/3 and 1/6 do not sum to exactly one, and "smoothed minus centre" would leak a
+// systematic change of sum(phi) into every step. The kernels march along z with the same x-y tiles as
+// the fused step (32 columns of which 30 are outputs, BY + 2 rows): every thread keeps three planes
+// of its own column in registers and applies the z filters there, one shared-memory plane holds the
+// z-filtered values, and the outputs apply the x-y filters from it.
 struct PhaseParams {
   int nx, ny, nz;
   long long N;
   double D, lambda, beta, kappa;
   double body[3];
   Scales sc;
+  int zchunk;
 };
 
-__device__ __forceinline__ long long site_of(int x, int y, int z, int nx, int ny) {
-  return ((long long)z * ny + y) * nx + x;
-}
+constexpr int kPhaseRows = 8;  // output rows per CTA of the phase-field kernels
 
-// phi_new from phi, u (decoded from the state) and G, all at time n
-template <class S, class T>
-__global__ void k_phase_advance(const S* __restrict__ st, const T* __restrict__ phi, const T* __restrict__ G,
-                                T* __restrict__ phi_new, PhaseParams p) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z * blockDim.z + threadIdx.z;
-  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  const long long N = p.N;
-  const long long s0 = site_of(x, y, z, p.nx, p.ny);
-  const T ph0 = phi[s0];
-  T div_adv = T(0), lap = T(0), div_g = T(0);
-  static_for<27>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    constexpr int cx = D3Q27::cx(q), cy = D3Q27::cy(q), cz = D3Q27::cz(q);
-    if constexpr (cx != 0 || cy != 0 || cz != 0) {
-      constexpr T w = T(D3Q27::w(q));
-      const int xs = wrap(x + cx, p.nx), ys = wrap(y + cy, p.ny), zs = wrap(z + cz, p.nz);
-      const long long s = site_of(xs, ys, zs, p.nx, p.ny);
-      const T ph = phi[s];
-      lap += w * (ph - ph0);
-      T ux, uy, uz;
-      if constexpr (Codec<S>::scaled) {
-        ux = Codec<S>::load(st + N + s) * p.sc.dec[1];
-        uy = Codec<S>::load(st + 2 * N + s) * p.sc.dec[1];
-        uz = Codec<S>::load(st + 3 * N + s) * p.sc.dec[1];
-      } else {
-        ux = st[N + s];
-        uy = st[2 * N + s];
-        uz = st[3 * N + s];
-      }
-      T cu = T(0), cg = T(0);
-      if constexpr (cx != 0) {
-        cu = sadd<cx>(cu, ph * ux);
-        cg = sadd<cx>(cg, G[s]);
-      }
-      if constexpr (cy != 0) {
-        cu = sadd<cy>(cu, ph * uy);
-        cg = sadd<cy>(cg, G[N + s]);
-      }
-      if constexpr (cz != 0) {
-        cu = sadd<cz>(cu, ph * uz);
-        cg = sadd<cz>(cg, G[2 * N + s]);
-      }
-      div_adv += w * cu;
-      div_g += w * cg;
-    }
-  });
-  phi_new[s0] = ph0 - T(3) * div_adv + T(p.D) * T(6) * lap - T(p.lambda) * T(3) * div_g;
-}
-
-// force F = mu grad phi + F^b and compression flux G from phi (time n+1)
 template <class T>
-__global__ void k_phase_forces(const T* __restrict__ phi, T* __restrict__ F, T* __restrict__ G, PhaseParams p) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z * blockDim.z + threadIdx.z;
-  if (x >= p.nx || y >= p.ny || z >= p.nz) return;
-  const long long N = p.N;
-  const long long s0 = site_of(x, y, z, p.nx, p.ny);
-  const T ph0 = phi[s0];
-  T gx = T(0), gy = T(0), gz = T(0), lap = T(0);
-  static_for<27>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    constexpr int cx = D3Q27::cx(q), cy = D3Q27::cy(q), cz = D3Q27::cz(q);
-    if constexpr (cx != 0 || cy != 0 || cz != 0) {
-      constexpr T w = T(D3Q27::w(q));
-      const int xs = wrap(x + cx, p.nx), ys = wrap(y + cy, p.ny), zs = wrap(z + cz, p.nz);
-      const T ph = phi[site_of(xs, ys, zs, p.nx, p.ny)];
-      lap += w * (ph - ph0);
-      if constexpr (cx != 0) gx = sadd<cx>(gx, w * ph);
-      if constexpr (cy != 0) gy = sadd<cy>(gy, w * ph);
-      if constexpr (cz != 0) gz = sadd<cz>(gz, w * ph);
+struct PhaseTile {
+  static constexpr int ROWS = kPhaseRows + 2;
+  static constexpr int SITES = ROWS * 32;
+  static constexpr T A0 = T(2) / T(3), A1 = T(1) / T(6);
+  // A_x A_y f and the two first differences D_x A_y f, D_y A_x f of the staged plane at site p
+  __device__ __forceinline__ static T axay(const T* f) {
+    const T r0 = A0 * f[0] + A1 * (f[-1] + f[1]);
+    const T rm = A0 * f[-32] + A1 * (f[-33] + f[-31]);
+    const T rp = A0 * f[32] + A1 * (f[31] + f[33]);
+    return A0 * r0 + A1 * (rm + rp);
+  }
+  __device__ __forceinline__ static T dxay(const T* f) {
+    return A1 * (A0 * (f[1] - f[-1]) + A1 * ((f[-31] - f[-33]) + (f[33] - f[31])));
+  }
+  __device__ __forceinline__ static T dyax(const T* f) {
+    return A1 * (A0 * (f[32] - f[-32]) + A1 * ((f[31] - f[-33]) + (f[33] - f[-31])));
+  }
+  // L_x A_y f + L_y f: the in-plane part of the Laplacian sum, zero on a constant field
+  __device__ __forceinline__ static T lap_xy(const T* f) {
+    const T am = A0 * f[-1] + A1 * (f[-33] + f[31]);
+    const T a0 = A0 * f[0] + A1 * (f[-32] + f[32]);
+    const T ap = A0 * f[1] + A1 * (f[-31] + f[33]);
+    return A1 * ((am - a0) + (ap - a0)) + A1 * ((f[-32] - f[0]) + (f[32] - f[0]));
+  }
+};
+
+// this thread's column of a phase-field kernel tile and its output flag
+struct PhaseColumn {
+  long long col;  // site index within a plane (periodically wrapped)
+  bool out;
+  int z0, z1;
+  __device__ __forceinline__ PhaseColumn(const PhaseParams& p) {
+    const int gx = int(blockIdx.x) * 30 - 1 + int(threadIdx.x);
+    const int gy = int(blockIdx.y) * kPhaseRows - 1 + int(threadIdx.y);
+    const int sx = ((gx % p.nx) + p.nx) % p.nx, sy = ((gy % p.ny) + p.ny) % p.ny;
+    col = (long long)sy * p.nx + sx;
+    out = threadIdx.y >= 1 && threadIdx.y <= kPhaseRows && threadIdx.x >= 1 && threadIdx.x <= 30 && gx < p.nx &&
+          gy < p.ny;
+    z0 = int(blockIdx.z) * p.zchunk;
+    z1 = min(p.nz, z0 + p.zchunk);
+  }
+};
+
+// phi_new from phi, u (decoded from the state) and G, all at time n:
+//   phi' = phi - 3 sum_i w_i c_i . V(x + c_i) + 6 D sum_i w_i (phi(x + c_i) - phi(x)),
+//   V = phi u + lambda G
+template <class S, class T>
+__global__ void __launch_bounds__(PhaseTile<T>::SITES) k_phase_advance(const S* __restrict__ st,
+                                                                       const T* __restrict__ phi,
+                                                                       const T* __restrict__ G,
+                                                                       T* __restrict__ phi_new, PhaseParams p) {
+  using PT = PhaseTile<T>;
+  __shared__ T sm[5][PT::SITES];  // phi, L_z phi, A_z V_x, A_z V_y, D_z V_z of the current plane
+  const PhaseColumn c(p);
+  const int me = threadIdx.y * 32 + threadIdx.x;
+  const long long N = p.N, plane = (long long)p.nx * p.ny;
+  const T lam = T(p.lambda), dif6 = T(6) * T(p.D);
+  // planes z-1, z, z+1 of this column: phi and V
+  T f[3], vx[3], vy[3], vz[3];
+  // raw values of the plane after those (prefetched)
+  T rph, rux, ruy, ruz, rgx, rgy, rgz;
+  auto fetch = [&](int zp) {
+    const long long s = (long long)wrap(zp, p.nz) * plane + c.col;  // zp in [-1, nz]
+    rph = phi[s];
+    if constexpr (Codec<S>::scaled) {
+      rux = T(Codec<S>::load(st + N + s) * p.sc.dec[1]);
+      ruy = T(Codec<S>::load(st + 2 * N + s) * p.sc.dec[1]);
+      ruz = T(Codec<S>::load(st + 3 * N + s) * p.sc.dec[1]);
+    } else {
+      rux = st[N + s];
+      ruy = st[2 * N + s];
+      ruz = st[3 * N + s];
     }
-  });
-  gx *= T(3);
-  gy *= T(3);
-  gz *= T(3);
-  lap *= T(6);
-  const T mu = T(4) * T(p.beta) * ph0 * (ph0 - T(1)) * (ph0 - T(0.5)) - T(p.kappa) * lap;
-  F[s0] = mu * gx + T(p.body[0]);
-  F[N + s0] = mu * gy + T(p.body[1]);
-  F[2 * N + s0] = mu * gz + T(p.body[2]);
-  T mag = sqrt(gx * gx + gy * gy + gz * gz);
-  mag = mag > T(1e-12) ? mag : T(1e-12);
-  const T c = ph0 * (T(1) - ph0) / mag;
-  G[s0] = c * gx;
-  G[N + s0] = c * gy;
-  G[2 * N + s0] = c * gz;
+    rgx = G[s];
+    rgy = G[N + s];
+    rgz = G[2 * N + s];
+  };
+  auto take = [&](int k) {
+    f[k] = rph;
+    vx[k] = rph * rux + lam * rgx;
+    vy[k] = rph * ruy + lam * rgy;
+    vz[k] = rph * ruz + lam * rgz;
+  };
+  fetch(c.z0 - 1);
+  take(0);
+  fetch(c.z0);
+  take(1);
+  fetch(c.z0 + 1);
+  for (int z = c.z0; z < c.z1; ++z) {
+    take(2);
+    if (z + 2 <= c.z1) fetch(z + 2);  // in flight during this plane
+    sm[0][me] = f[1];
+    sm[1][me] = PT::A1 * ((f[0] - f[1]) + (f[2] - f[1]));
+    sm[2][me] = PT::A0 * vx[1] + PT::A1 * (vx[0] + vx[2]);
+    sm[3][me] = PT::A0 * vy[1] + PT::A1 * (vy[0] + vy[2]);
+    sm[4][me] = PT::A1 * (vz[2] - vz[0]);
+    __syncthreads();
+    if (c.out) {
+      const T div = PT::dxay(sm[2] + me) + PT::dyax(sm[3] + me) + PT::axay(sm[4] + me);
+      const T lap = PT::lap_xy(sm[0] + me) + PT::axay(sm[1] + me);
+      phi_new[(long long)z * plane + c.col] = f[1] - T(3) * div + dif6 * lap;
+    }
+    __syncthreads();
+    f[0] = f[1];
+    f[1] = f[2];
+    vx[0] = vx[1];
+    vx[1] = vx[2];
+    vy[0] = vy[1];
+    vy[1] = vy[2];
+    vz[0] = vz[1];
+    vz[1] = vz[2];
+  }
+}
+
+// force F = mu grad phi + F^b and compression flux G from phi (time n+1):
+//   grad phi = 3 (D_x A_y A_z, D_y A_x A_z, D_z A_x A_y) phi, lap phi = 6 (A_x A_y A_z phi - phi),
+//   mu = 4 beta phi (phi - 1)(phi - 1/2) - kappa lap phi
+template <class T>
+__global__ void __launch_bounds__(PhaseTile<T>::SITES) k_phase_forces(const T* __restrict__ phi,
+                                                                      T* __restrict__ F, T* __restrict__ G,
+                                                                      PhaseParams p) {
+  using PT = PhaseTile<T>;
+  __shared__ T sm[4][PT::SITES];  // A_z phi, D_z phi, phi, L_z phi of the current plane
+  const PhaseColumn c(p);
+  const int me = threadIdx.y * 32 + threadIdx.x;
+  const long long N = p.N, plane = (long long)p.nx * p.ny;
+  const T beta4 = T(4) * T(p.beta), kappa = T(p.kappa);
+  const T b0 = T(p.body[0]), b1 = T(p.body[1]), b2 = T(p.body[2]);
+  auto fetch = [&](int zp) { return phi[(long long)wrap(zp, p.nz) * plane + c.col]; };  // zp in [-1, nz]
+  T f0 = fetch(c.z0 - 1), f1 = fetch(c.z0), f2, nxt = fetch(c.z0 + 1);
+  for (int z = c.z0; z < c.z1; ++z) {
+    f2 = nxt;
+    if (z + 2 <= c.z1) nxt = fetch(z + 2);
+    sm[0][me] = PT::A0 * f1 + PT::A1 * (f0 + f2);
+    sm[1][me] = PT::A1 * (f2 - f0);
+    sm[2][me] = f1;
+    sm[3][me] = PT::A1 * ((f0 - f1) + (f2 - f1));
+    __syncthreads();
+    if (c.out) {
+      const T gx = T(3) * PT::dxay(sm[0] + me), gy = T(3) * PT::dyax(sm[0] + me), gz = T(3) * PT::axay(sm[1] + me);
+      const T lap = T(6) * (PT::lap_xy(sm[2] + me) + PT::axay(sm[3] + me));
+      const T mu = beta4 * f1 * (f1 - T(1)) * (f1 - T(0.5)) - kappa * lap;
+      const long long s = (long long)z * plane + c.col;
+      F[s] = mu * gx + b0;
+      F[N + s] = mu * gy + b1;
+      F[2 * N + s] = mu * gz + b2;
+      // phi (1 - phi) / max(|grad phi|, 1e-12)
+      const T g2 = gx * gx + gy * gy + gz * gz;
+      const T cc = f1 * (T(1) - f1) * rsqrt(g2 > T(1e-24) ? g2 : T(1e-24));
+      G[s] = cc * gx;
+      G[N + s] = cc * gy;
+      G[2 * N + s] = cc * gz;
+    }
+    __syncthreads();
+    f0 = f1;
+    f1 = f2;
+  }
 }
 
 }  // namespace lbf

@@ -24,7 +24,7 @@ struct KernelInfo {
 
 template <class L, class S, bool MASK, bool TWO, bool FF, bool TMA>
 KernelInfo fwd_info() {
-  constexpr int BY = fwd_rows(L::Q, std::is_same<S, double>::value);
+  constexpr int BY = fwd_rows(L::Q, int(sizeof(S)));
   KernelInfo k;
   k.fn = reinterpret_cast<const void*>(&k_stream_collide<L, S, BY, MASK, TWO, FF, TMA>);
   k.smem = fwd_smem_bytes<L, S, BY, MASK, TMA>();

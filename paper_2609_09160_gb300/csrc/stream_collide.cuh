@@ -289,15 +289,21 @@ struct SiteExtra {
   bool solid;
 };
 
-// output rows per CTA (FP32 compute per lattice, FP64 compute) and the minimum resident CTAs per
-// SM asked of the register allocator. D3Q19 FP32: 8 rows, 3 CTAs of 320 threads (<= 64
-// registers), limited by shared memory to 3; D3Q27: its larger ring fits 2 CTAs, so 2 (<= 96
-// registers).
+// output rows per CTA and the minimum resident CTAs per SM asked of the register allocator, per
+// lattice and storage width (bytes per stored value). D3Q19 FP32: 8 rows, 3 CTAs of 320 threads
+// (<= 64 registers), limited by shared memory to 3. D3Q27: its larger ring fits 2 CTAs of 8 rows
+// (<= 96 registers); with 16-bit storage the TMA stages are half as large and 6-row CTAs fit 3.
 #ifndef LBF_FWD_ROWS_Q19
 #define LBF_FWD_ROWS_Q19 8
 #endif
 #ifndef LBF_FWD_ROWS_Q27
 #define LBF_FWD_ROWS_Q27 8
+#endif
+#ifndef LBF_FWD_ROWS_Q19_16
+#define LBF_FWD_ROWS_Q19_16 8
+#endif
+#ifndef LBF_FWD_ROWS_Q27_16
+#define LBF_FWD_ROWS_Q27_16 8
 #endif
 #ifndef LBF_FWD_ROWS_F64
 #define LBF_FWD_ROWS_F64 4
@@ -308,15 +314,27 @@ struct SiteExtra {
 #ifndef LBF_FWD_MINB_Q27
 #define LBF_FWD_MINB_Q27 2
 #endif
-constexpr int fwd_rows(int Q, bool fp64) {
-  return fp64 ? LBF_FWD_ROWS_F64 : (Q == 19 ? LBF_FWD_ROWS_Q19 : LBF_FWD_ROWS_Q27);
+#ifndef LBF_FWD_MINB_Q19_16
+#define LBF_FWD_MINB_Q19_16 3
+#endif
+#ifndef LBF_FWD_MINB_Q27_16
+#define LBF_FWD_MINB_Q27_16 2
+#endif
+constexpr int fwd_rows(int Q, int bytes) {
+  return bytes == 8 ? LBF_FWD_ROWS_F64
+                    : (bytes == 4 ? (Q == 19 ? LBF_FWD_ROWS_Q19 : LBF_FWD_ROWS_Q27)
+                                  : (Q == 19 ? LBF_FWD_ROWS_Q19_16 : LBF_FWD_ROWS_Q27_16));
 }
-constexpr int fwd_minb(int Q, bool fp64) { return fp64 ? 1 : (Q == 19 ? LBF_FWD_MINB_Q19 : LBF_FWD_MINB_Q27); }
+constexpr int fwd_minb(int Q, int bytes) {
+  return bytes == 8 ? 1
+                    : (bytes == 4 ? (Q == 19 ? LBF_FWD_MINB_Q19 : LBF_FWD_MINB_Q27)
+                                  : (Q == 19 ? LBF_FWD_MINB_Q19_16 : LBF_FWD_MINB_Q27_16));
+}
 
 constexpr uint32_t kWaitPolls = 1u << 20;  // bound of every mbarrier wait
 
 template <class L, class S, int BY, bool MASK, bool TWO, bool FF, bool TMA>
-__global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, std::is_same<S, double>::value))
+__global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeof(S))))
     k_stream_collide(const FwdParams a, const __grid_constant__ CUtensorMap tmap) {
   using T = typename ComputeOf<S>::type;
   using D = Dirs<L>;
@@ -458,7 +476,10 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, std::is_s
 
   // own-site values of the planes being output (carried from staging)
   T Fown[3] = {Fu0, Fu1, Fu2}, Fnext[3] = {Fu0, Fu1, Fu2};
-  T i2r_own = T(0.5), i2r_next = T(0.5);
+  // two components at equal densities: 1/(2 rho), and nu_l, nu_h - nu_l with the rate at nu_l
+  const T i2r_two = TWO ? T(0.5) / pick<T>(a.rho_l, a.rho_l_f) : T(0.5);
+  const T nu_l_two = pick<T>(a.nu_l, a.nu_l_f), dnu_two = pick<T>(a.nu_h - a.nu_l, a.dnu_f);
+  const T omm_two = T(1) - T(1) / (T(3) * nu_l_two + T(0.5));
   T phi_own = T(0), phi_next = T(0);
   // axial populations of the own column: up(z-1), up(z), dn(z), rest(z) and the new plane's
   T up_m1 = T(0), up_0 = T(0), dn_0 = T(0), rest_0 = T(0);
@@ -476,14 +497,13 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, std::is_s
     read_raw(p, par, m);
     T inv2rho = T(0.5), omm = one_m_omega;
     if constexpr (TWO) {
-      const T rho_l = pick<T>(a.rho_l, a.rho_l_f), drho = pick<T>(a.rho_h - a.rho_l, a.drho_f);
-      const T rho = rho_l + e.phi_o * drho;
-      const T nu = pick<T>(a.nu_l, a.nu_l_f) + e.phi_o * pick<T>(a.nu_h - a.nu_l, a.dnu_f);
-      inv2rho = T(0.5) / rho;
-      omm = T(1) - T(1) / (T(3) * nu + T(0.5));
+      // equal densities (the only two-component case built): 1/(2 rho) is a constant; the
+      // relaxation rate follows nu(phi) = nu_l + phi (nu_h - nu_l) when the phases differ
+      inv2rho = i2r_two;
+      if (dnu_two != T(0)) omm = T(1) - T(1) / (T(3) * (nu_l_two + e.phi_o * dnu_two) + T(0.5));
+      else omm = omm_two;
       if (outcol) {
         phi_next = e.phi_n;
-        i2r_next = T(0.5) / (rho_l + e.phi_n * drho);
         Fnext[0] = e.Fn[0];
         Fnext[1] = e.Fn[1];
         Fnext[2] = e.Fn[2];
@@ -580,7 +600,6 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, std::is_s
   Fown[0] = Fnext[0];
   Fown[1] = Fnext[1];
   Fown[2] = Fnext[2];
-  i2r_own = i2r_next;
   phi_own = phi_next;
   load_extra(z0 + 1, ex);
   if constexpr (MASK)
@@ -661,7 +680,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, std::is_s
         A = gather(std::false_type{});
       }
       // Eq. (corr): u = a1 + F/(2 rho), a2 = (sum c c f - cs2 a0 delta) + (u F + F u)/(2 rho)
-      const T i2r = i2r_own;
+      const T i2r = i2r_two;
       const T hx = (SITEF ? Fown[0] : Fu0) * i2r, hy = (SITEF ? Fown[1] : Fu1) * i2r,
               hz = (SITEF ? Fown[2] : Fu2) * i2r;
       const T ux = A.jx + hx, uy = A.jy + hy, uz = A.jz + hz;
@@ -706,7 +725,6 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, std::is_s
     Fown[0] = Fnext[0];
     Fown[1] = Fnext[1];
     Fown[2] = Fnext[2];
-    i2r_own = i2r_next;
     phi_own = phi_next;
     any_m = any_0;
     any_0 = any_p;
