@@ -343,6 +343,19 @@ def extras(torch, device, quick):
     return out
 
 
+def max_over_ranks(torch, dist, t, device):
+    """The job's time: the slowest rank's (every rank gets it)."""
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return tt.item()
+
+
+def replicas_mlups(world, sites_per_rank, steps, t):
+    """Whole-job throughput of `world` independent replicas of `sites_per_rank` sites, `steps`
+    steps each, finished after `t` seconds (weak scaling: the work per rank is fixed)."""
+    return world * sites_per_rank * steps / t / 1e6
+
+
 def run_ours(args):
     import torch
 
@@ -377,11 +390,9 @@ def run_ours(args):
         t = time_steps(torch, s, args.steps, args.warmup, barrier)
     clocks = clk.summary()
     if world > 1:
-        tt = torch.tensor([t], dtype=torch.float64, device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = tt.item()
+        t = max_over_ranks(torch, dist, t, device)
     n = s.N
-    value = world * n * args.steps / t / 1e6
+    value = replicas_mlups(world, n, args.steps, t)
     sums = s.reduce()
     if rank != 0:
         if dist is not None:
