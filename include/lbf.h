@@ -18,10 +18,11 @@
  *  - Internal state ("state buffer"): the same 10 fields in the storage dtype, with the tensor
  *    stored as N = A - u u and, for 16-bit storage, every group multiplied by a power of two.
  *    Callers treat it as opaque bytes of size lbf_state_bytes().
- *  - 16-bit storage: a time step rounds the values it stores stochastically (unbiased), with
- *    random bits from a counter-based generator keyed by the site and the context's count of
- *    steps taken, so results are bitwise reproducible for the same sequence of calls. Loading a
- *    state (lbf_set_moments) rounds to nearest.
+ *  - 16-bit storage: by default a time step rounds the values it stores stochastically
+ *    (unbiased), with random bits from a counter-based generator keyed by the site and the
+ *    context's count of steps taken, so results are bitwise reproducible for the same sequence of
+ *    calls; lbf_params.rounding selects round-to-nearest instead. Loading a state
+ *    (lbf_set_moments) always rounds to nearest.
  *  - Every call is ordered on the context's CUDA stream (lbf_params.stream) and returns without
  *    waiting for the GPU, except lbf_reduce and lbf_synchronize, which wait for the stream.
  *  - The library allocates no device memory: the caller provides one workspace of
@@ -47,6 +48,12 @@ enum { LBF_D3Q19 = 19, LBF_D3Q27 = 27 };
 
 /* storage / transfer dtypes; F64 storage computes in FP64, every other storage in FP32 */
 enum { LBF_F64 = 0, LBF_F32 = 1, LBF_F16 = 2, LBF_BF16 = 3 };
+
+/* rounding of the values a time step stores in 16-bit storage (not in the paper, which has no
+   16-bit storage). Round-to-nearest discards every update smaller than half a unit in the last
+   place, so a slowly evolving flow freezes in place on large lattices; stochastic rounding keeps
+   the expected stored value exact. */
+enum { LBF_ROUND_STOCHASTIC = 0, LBF_ROUND_NEAREST = 1 };
 
 typedef enum {
   LBF_OK = 0,
@@ -82,6 +89,8 @@ typedef struct {
   double scale_hint[3]; /* 16-bit storage: expected max |p*|, |u|, |A - u u|; 0 = take each from
                            the state given to lbf_set_moments */
   void* stream;         /* cudaStream_t used for every call; NULL = legacy default stream */
+  int rounding;         /* LBF_ROUND_STOCHASTIC (0, default) or LBF_ROUND_NEAREST: 16-bit stores of
+                           a time step; ignored for FP32/FP64 storage */
 } lbf_params;
 
 /* Workspace bytes the context needs for these parameters, 0 if the parameters are invalid.

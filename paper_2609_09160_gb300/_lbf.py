@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(_PKG, "liblbf.so")
 LBF_D3Q19, LBF_D3Q27 = 19, 27
 LBF_F64, LBF_F32, LBF_F16, LBF_BF16 = 0, 1, 2, 3
 LBF_OK, LBF_EINVAL, LBF_ENOMEM, LBF_ECUDA, LBF_EUNSTABLE, LBF_EINTERNAL, LBF_ENOTSUP = range(7)
+LBF_ROUND_STOCHASTIC, LBF_ROUND_NEAREST = 0, 1
 
 # every symbol declared in include/lbf.h
 EXPORTS = ("lbf_workspace_bytes", "lbf_validate", "lbf_create", "lbf_set_moments", "lbf_step", "lbf_moments",
@@ -26,6 +27,7 @@ class lbf_params(ctypes.Structure):
         ("rho_l", ctypes.c_double), ("rho_h", ctypes.c_double), ("tau_l", ctypes.c_double),
         ("tau_h", ctypes.c_double), ("sigma", ctypes.c_double), ("width", ctypes.c_double),
         ("diffusivity", ctypes.c_double), ("scale_hint", ctypes.c_double * 3), ("stream", ctypes.c_void_p),
+        ("rounding", ctypes.c_int),
     ]
 
 

@@ -70,6 +70,8 @@ lbf_status check_params(const lbf_params* p) {
   const double n = double(p->nx) * double(p->ny) * double(p->nz);
   if (n > 4.0e10) return fail(LBF_EINVAL, "lattice too large");
   if (storage_bytes(p->storage) == 0) return fail(LBF_EINVAL, "storage must be LBF_F64, LBF_F32, LBF_F16 or LBF_BF16");
+  if (p->rounding != LBF_ROUND_STOCHASTIC && p->rounding != LBF_ROUND_NEAREST)
+    return fail(LBF_EINVAL, "rounding must be LBF_ROUND_STOCHASTIC or LBF_ROUND_NEAREST");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(p->force[a])) return fail(LBF_EINVAL, "force must be finite");
   if (p->two_component) {
@@ -357,6 +359,7 @@ FwdParams forward_params(const lbf_ctx* c, const void* src, void* dst, bool redu
   a.zchunk = c->zchunk;
   a.umax2 = 0.16f;
   a.salt = fmix32(uint32_t(c->steps_done) * 0x9E3779B9u + 0x7F4A7C15u);
+  a.round_nearest = c->prm.rounding == LBF_ROUND_NEAREST;
   set_fp32_copies(a);
   return a;
 }

@@ -58,6 +58,7 @@ struct FwdParams {
   int zchunk;
   float umax2;
   uint32_t salt;            // per-step word mixed into the stochastic rounding of 16-bit storage
+  int round_nearest;        // 16-bit storage: round to nearest instead of stochastically
   // FP32 copies of the double scalars above (set_fp32_copies), read by the FP32-compute kernels
   float force_f[3], omega_f, rho_l_f, drho_f, nu_l_f, dnu_f;
 };
@@ -91,10 +92,13 @@ __device__ __forceinline__ T ld_field(const S* base, long long idx, float dec) {
 // one field of a time step's output: 16-bit storage is scaled and rounded stochastically with the
 // next word of the site's random sequence rs
 template <class S, class T>
-__device__ __forceinline__ void st_field(S* base, long long idx, T v, float enc, uint32_t& rs) {
+__device__ __forceinline__ void st_field(S* base, long long idx, T v, float enc, uint32_t& rs, bool nearest) {
   if constexpr (Codec<S>::scaled) {
     rs = lcg_next(rs);
-    Codec<S>::store_sr(base + idx, static_cast<float>(v) * enc, rs);
+    if (nearest)
+      Codec<S>::store(base + idx, static_cast<float>(v) * enc);
+    else
+      Codec<S>::store_sr(base + idx, static_cast<float>(v) * enc, rs);
   } else {
     Codec<S>::store(base + idx, v);
   }
@@ -696,16 +700,17 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
         const long long zc = (long long)z * plane + col;
         // random sequence of this site and step (16-bit storage only)
         uint32_t rs = Codec<S>::scaled ? fmix32(uint32_t(zc) ^ a.salt) : 0u;
-        st_field<S, T>(dst, zc, A.a0, a.sc.enc[0], rs);
-        st_field<S, T>(dst + N, zc, ux, a.sc.enc[1], rs);
-        st_field<S, T>(dst + 2 * N, zc, uy, a.sc.enc[1], rs);
-        st_field<S, T>(dst + 3 * N, zc, uz, a.sc.enc[1], rs);
-        st_field<S, T>(dst + 4 * N, zc, nxx, a.sc.enc[2], rs);
-        st_field<S, T>(dst + 5 * N, zc, nyy, a.sc.enc[2], rs);
-        st_field<S, T>(dst + 6 * N, zc, nzz, a.sc.enc[2], rs);
-        st_field<S, T>(dst + 7 * N, zc, nxy, a.sc.enc[2], rs);
-        st_field<S, T>(dst + 8 * N, zc, nxz, a.sc.enc[2], rs);
-        st_field<S, T>(dst + 9 * N, zc, nyz, a.sc.enc[2], rs);
+        const bool rn = a.round_nearest != 0;
+        st_field<S, T>(dst, zc, A.a0, a.sc.enc[0], rs, rn);
+        st_field<S, T>(dst + N, zc, ux, a.sc.enc[1], rs, rn);
+        st_field<S, T>(dst + 2 * N, zc, uy, a.sc.enc[1], rs, rn);
+        st_field<S, T>(dst + 3 * N, zc, uz, a.sc.enc[1], rs, rn);
+        st_field<S, T>(dst + 4 * N, zc, nxx, a.sc.enc[2], rs, rn);
+        st_field<S, T>(dst + 5 * N, zc, nyy, a.sc.enc[2], rs, rn);
+        st_field<S, T>(dst + 6 * N, zc, nzz, a.sc.enc[2], rs, rn);
+        st_field<S, T>(dst + 7 * N, zc, nxy, a.sc.enc[2], rs, rn);
+        st_field<S, T>(dst + 8 * N, zc, nxz, a.sc.enc[2], rs, rn);
+        st_field<S, T>(dst + 9 * N, zc, nyz, a.sc.enc[2], rs, rn);
         if (!(uu <= T(a.umax2))) atomicOr(a.flags, 1u);
         red[0] += A.a0;
         red[1] += ux;

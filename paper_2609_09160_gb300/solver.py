@@ -31,7 +31,7 @@ class Solver:
     """
 
     def __init__(self, shape, lattice=19, tau=0.8, storage="f32", force=(0.0, 0.0, 0.0), force_field=None,
-                 mask=None, two_component=None, scale_hint=None, device=None):
+                 mask=None, two_component=None, scale_hint=None, rounding="stochastic", device=None):
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
         self.device = torch.device(device if device is not None else "cuda")
@@ -67,6 +67,7 @@ class Solver:
         if scale_hint is not None:
             for a in range(3):
                 p.scale_hint[a] = float(scale_hint[a])
+        p.rounding = {"stochastic": _lbf.LBF_ROUND_STOCHASTIC, "nearest": _lbf.LBF_ROUND_NEAREST}[rounding]
         with torch.cuda.device(self.device):
             self.stream = torch.cuda.current_stream(self.device)
             p.stream = self.stream.cuda_stream

@@ -3,6 +3,8 @@ entry points (validation, workspace layout, status strings) behave as documented
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -33,6 +35,25 @@ def test_every_declared_symbol_is_exported(lib):
         assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
 
 
+def test_binding_struct_layout_matches_the_header(tmp_path):
+    """The ctypes lbf_params has the C struct's size and field offsets (compiled with the host C
+    compiler against include/lbf.h)."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    fields = [f for f, _ in _lbf.lbf_params._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbf.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(lbf_params));\n' +
+                   "".join(f'  printf("%zu\\n", offsetof(lbf_params, {f}));\n' for f in fields) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(_lbf.lbf_params)] + [getattr(_lbf.lbf_params, f).offset for f in fields]
+    assert got == want
+
+
 def params(**kw):
     p = _lbf.lbf_params()
     p.lattice, p.nx, p.ny, p.nz, p.storage, p.tau = 19, 16, 16, 16, _lbf.LBF_F32, 0.8
@@ -57,6 +78,7 @@ def test_workspace_holds_two_moment_buffers(lib):
     (dict(nx=0), _lbf.LBF_EINVAL),
     (dict(tau=0.5), _lbf.LBF_EINVAL),
     (dict(storage=7), _lbf.LBF_EINVAL),
+    (dict(rounding=2), _lbf.LBF_EINVAL),
     (dict(two_component=1, tau_l=1.0, tau_h=1.0, rho_l=0.5, rho_h=1.5, width=4.0, sigma=0.03, diffusivity=0.1),
      _lbf.LBF_ENOTSUP),
     (dict(two_component=1, tau_l=1.0, tau_h=0.4, rho_l=1.0, rho_h=1.0, width=4.0, sigma=0.03, diffusivity=0.1),

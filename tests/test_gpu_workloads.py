@@ -61,17 +61,18 @@ def _velocity_errors(M, ref):
 def test_16bit_deviation_storage_d3q27_taylor_green_64():
     """D3Q27, 64^3 periodic Taylor-Green (U0 = 0.04) plus a random-phase perturbation of RMS 0.01,
     tau = 0.55, 500 steps, every storage dtype against FP64 storage on the same GPU. Velocity
-    error, relative in the L2 norm over the box: FP32 < 1e-5, FP16 < 1e-3 (measured 4.8e-4; in
-    the max norm over sites FP16 reaches 2.2e-3, bounded here by 5e-3), BF16 < 0.1 (measured
-    7.5e-2: 8 significand bits)."""
+    error, relative in the L2 norm over the box: FP32 < 1e-5, FP16 < 1e-3 (measured 5.8e-4 with
+    the default stochastic rounding, 4.8e-4 with round-to-nearest; in the max norm over sites FP16
+    reaches ~2e-3, bounded here by 5e-3), BF16 < 1e-2 (measured 4.7e-3; 8 significand bits)."""
     n, tau, steps = 64, 0.55, 500
     M0 = synth.taylor_green_perturbed(n, 0.04, tau, 0.01, seed=3, dtype=torch.float64, device="cuda")
     out = {}
-    for st in ("f64", "f32", "f16", "bf16"):
-        s = Solver((n, n, n), lattice=27, tau=tau, storage=st)
+    for key, st, rounding in (("f64", "f64", "stochastic"), ("f32", "f32", "stochastic"), ("f16", "f16", "stochastic"),
+                              ("bf16", "bf16", "stochastic"), ("f16rn", "f16", "nearest")):
+        s = Solver((n, n, n), lattice=27, tau=tau, storage=st, rounding=rounding)
         s.set_moments(M0 if st == "f64" else M0.float())
         s.step(steps)
-        out[st] = s.moments()
+        out[key] = s.moments()
         del s
     ref = out["f64"]
     l2, mx = _velocity_errors(out["f32"], ref)
@@ -79,22 +80,28 @@ def test_16bit_deviation_storage_d3q27_taylor_green_64():
     l2, mx = _velocity_errors(out["f16"], ref)
     assert l2 < 1e-3 and mx < 5e-3, (l2, mx)
     l2, mx = _velocity_errors(out["bf16"], ref)
-    assert l2 < 0.1, (l2, mx)
+    assert l2 < 1e-2, (l2, mx)
+    l2, mx = _velocity_errors(out["f16rn"], ref)
+    assert l2 < 1e-3 and mx < 5e-3, (l2, mx)
 
 
 @pytest.mark.slow
 def test_16bit_deviation_storage_d3q27_taylor_green_512_crop():
     """The full-size configuration: D3Q27, 512^3 Taylor-Green + perturbation, tau = 0.55, 500
-    steps, errors of FP32 and FP16 storage against FP64 storage on a 64^3 crop."""
+    steps, errors of FP32 and FP16 storage against FP64 storage on a 64^3 crop. With the default
+    stochastic rounding FP16 stays below 1e-3 (measured 5.9e-4); round-to-nearest (the survey's
+    reading, LBF_ROUND_NEAREST) lets the slowly evolving flow freeze and exceeds 2e-3 (measured
+    8.0e-3), which this test also pins so that a silent loss of the stochastic path shows."""
     n, tau, steps = 512, 0.55, 500
     crop = (slice(None), slice(0, 64), slice(0, 64), slice(0, 64))
     M0 = synth.taylor_green_perturbed(n, 0.04, tau, 0.01, seed=3, dtype=torch.float32, device="cuda")
     out = {}
-    for st in ("f64", "f32", "f16"):
-        s = Solver((n, n, n), lattice=27, tau=tau, storage=st)
+    for key, st, rounding in (("f64", "f64", "stochastic"), ("f32", "f32", "stochastic"),
+                              ("f16", "f16", "stochastic"), ("f16rn", "f16", "nearest")):
+        s = Solver((n, n, n), lattice=27, tau=tau, storage=st, rounding=rounding)
         s.set_moments(M0)
         s.step(steps)
-        out[st] = s.moments()[crop].clone()
+        out[key] = s.moments()[crop].clone()
         del s
         torch.cuda.empty_cache()
     ref = out["f64"]
@@ -102,6 +109,8 @@ def test_16bit_deviation_storage_d3q27_taylor_green_512_crop():
     assert l2 < 1e-5 and mx < 1e-5, (l2, mx)
     l2, mx = _velocity_errors(out["f16"], ref)
     assert l2 < 1e-3 and mx < 5e-3, (l2, mx)
+    l2_rn, _ = _velocity_errors(out["f16rn"], ref)
+    assert l2_rn > 2e-3, l2_rn
 
 
 def test_droplet_128_laplace_law_and_conservation():
