@@ -175,8 +175,8 @@ struct lbf_ctx {
 
 namespace {
 
-KernelInfo forward_for(int Q, int storage, bool mask, bool two, bool field, bool tma) {
-  return forward_kernel_for(Q, storage, mask, two, field, tma);
+KernelInfo forward_for(int Q, int storage, bool mask, bool two, bool field, bool tma, bool nearest) {
+  return forward_kernel_for(Q, storage, mask, two, field, tma, nearest);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -359,7 +359,6 @@ FwdParams forward_params(const lbf_ctx* c, const void* src, void* dst, bool redu
   a.zchunk = c->zchunk;
   a.umax2 = 0.16f;
   a.salt = fmix32(uint32_t(c->steps_done) * 0x9E3779B9u + 0x7F4A7C15u);
-  a.round_nearest = c->prm.rounding == LBF_ROUND_NEAREST;
   set_fp32_copies(a);
   return a;
 }
@@ -542,7 +541,8 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   set_scales(c, m0);
 
   c->tma = tma_eligible(c->storage, c->nx);
-  c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two, params->force_field != nullptr, c->tma);
+  c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two, params->force_field != nullptr, c->tma,
+                       params->rounding == LBF_ROUND_NEAREST);
   c->adj = adjoint_for(c->Q, c->storage, c->has_mask);
   if (c->fwd.fn == nullptr) {
     delete c;

@@ -22,11 +22,11 @@ struct KernelInfo {
   int box_x;        // TMA box width in elements (0: the kernel loads without TMA)
 };
 
-template <class L, class S, bool MASK, bool TWO, bool FF, bool TMA>
+template <class L, class S, bool MASK, bool TWO, bool FF, bool TMA, bool RN>
 KernelInfo fwd_info() {
   constexpr int BY = fwd_rows(L::Q, int(sizeof(S)));
   KernelInfo k;
-  k.fn = reinterpret_cast<const void*>(&k_stream_collide<L, S, BY, MASK, TWO, FF, TMA>);
+  k.fn = reinterpret_cast<const void*>(&k_stream_collide<L, S, BY, MASK, TWO, FF, TMA, RN>);
   k.smem = fwd_smem_bytes<L, S, BY, MASK, TMA>();
   k.threads = FwdTile<BY>::THREADS;
   k.by = BY;
@@ -47,23 +47,31 @@ KernelInfo adj_info() {
   return k;
 }
 
-// forward kernel of lattice L and storage S for (mask, two-component, force field, TMA); fn ==
-// nullptr for combinations that are not built (two-component with a mask or a force field)
-template <class L, class S, bool TMA>
+// forward kernel of lattice L and storage S for (mask, two-component, force field, TMA, 16-bit
+// round-to-nearest); fn == nullptr for combinations that are not built (two-component with a mask
+// or a force field). Round-to-nearest kernels exist for 16-bit storage only (FP32/FP64 stores
+// are exact).
+template <class L, class S, bool TMA, bool RN>
 KernelInfo forward_kernel_s(bool mask, bool two, bool field) {
-  if (two) return (mask || field) ? KernelInfo{nullptr, 0, 0, 0, 0} : fwd_info<L, S, false, true, false, TMA>();
-  if (mask) return field ? fwd_info<L, S, true, false, true, TMA>() : fwd_info<L, S, true, false, false, TMA>();
-  return field ? fwd_info<L, S, false, false, true, TMA>() : fwd_info<L, S, false, false, false, TMA>();
+  if (two) return (mask || field) ? KernelInfo{nullptr, 0, 0, 0, 0} : fwd_info<L, S, false, true, false, TMA, RN>();
+  if (mask) return field ? fwd_info<L, S, true, false, true, TMA, RN>() : fwd_info<L, S, true, false, false, TMA, RN>();
+  return field ? fwd_info<L, S, false, false, true, TMA, RN>() : fwd_info<L, S, false, false, false, TMA, RN>();
 }
 
 template <class L, class S>
-KernelInfo forward_kernel_ls(bool mask, bool two, bool field, bool tma) {
-  return tma ? forward_kernel_s<L, S, true>(mask, two, field) : forward_kernel_s<L, S, false>(mask, two, field);
+KernelInfo forward_kernel_ls(bool mask, bool two, bool field, bool tma, bool nearest) {
+  if constexpr (Codec<S>::scaled) {
+    if (nearest)
+      return tma ? forward_kernel_s<L, S, true, true>(mask, two, field)
+                 : forward_kernel_s<L, S, false, true>(mask, two, field);
+  }
+  return tma ? forward_kernel_s<L, S, true, false>(mask, two, field)
+             : forward_kernel_s<L, S, false, false>(mask, two, field);
 }
 
 // entry points implemented per (lattice, storage) translation unit
 #define LBF_DECLARE_TU(q, s)                                                             \
-  KernelInfo forward_kernel_q##q##_s##s(bool mask, bool two, bool field, bool tma); \
+  KernelInfo forward_kernel_q##q##_s##s(bool mask, bool two, bool field, bool tma, bool nearest); \
   KernelInfo adjoint_kernel_q##q##_s##s(bool mask);
 LBF_DECLARE_TU(19, 0)
 LBF_DECLARE_TU(19, 1)
@@ -75,13 +83,18 @@ LBF_DECLARE_TU(27, 2)
 LBF_DECLARE_TU(27, 3)
 #undef LBF_DECLARE_TU
 
-inline KernelInfo forward_kernel_for(int lattice, int storage, bool mask, bool two, bool field, bool tma) {
+inline KernelInfo forward_kernel_for(int lattice, int storage, bool mask, bool two, bool field, bool tma,
+                                     bool nearest) {
   const bool q19 = lattice == 19;
   switch (storage) {
-    case ST_F64: return q19 ? forward_kernel_q19_s0(mask, two, field, tma) : forward_kernel_q27_s0(mask, two, field, tma);
-    case ST_F32: return q19 ? forward_kernel_q19_s1(mask, two, field, tma) : forward_kernel_q27_s1(mask, two, field, tma);
-    case ST_F16: return q19 ? forward_kernel_q19_s2(mask, two, field, tma) : forward_kernel_q27_s2(mask, two, field, tma);
-    case ST_BF16: return q19 ? forward_kernel_q19_s3(mask, two, field, tma) : forward_kernel_q27_s3(mask, two, field, tma);
+    case ST_F64:
+      return q19 ? forward_kernel_q19_s0(mask, two, field, tma, nearest) : forward_kernel_q27_s0(mask, two, field, tma, nearest);
+    case ST_F32:
+      return q19 ? forward_kernel_q19_s1(mask, two, field, tma, nearest) : forward_kernel_q27_s1(mask, two, field, tma, nearest);
+    case ST_F16:
+      return q19 ? forward_kernel_q19_s2(mask, two, field, tma, nearest) : forward_kernel_q27_s2(mask, two, field, tma, nearest);
+    case ST_BF16:
+      return q19 ? forward_kernel_q19_s3(mask, two, field, tma, nearest) : forward_kernel_q27_s3(mask, two, field, tma, nearest);
   }
   return KernelInfo{nullptr, 0, 0, 0, 0};
 }

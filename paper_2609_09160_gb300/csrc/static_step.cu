@@ -107,7 +107,7 @@ extern "C" lbf_status lbf_step_static(const lbf_params* params, const void* src,
   PFN_cuTensorMapEncodeTiled_v12000 enc = static_encoder();
   const bool tma = enc != nullptr && (size_t(nx) * es) % 16 == 0 && std::getenv("LBF_NO_TMA") == nullptr;
   const KernelInfo k = forward_kernel_for(params->lattice, params->storage, mask_device != nullptr, false,
-                                          params->force_field != nullptr, tma);
+                                          params->force_field != nullptr, tma, false);
   if (k.fn == nullptr) return fail(LBF_ENOTSUP, "no kernel for this combination");
 
   // grid: 30 x by output columns per CTA, z-chunks of about 32 planes, at most kStaticMaxBlocks CTAs

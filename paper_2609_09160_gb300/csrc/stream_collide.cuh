@@ -58,7 +58,6 @@ struct FwdParams {
   int zchunk;
   float umax2;
   uint32_t salt;            // per-step word mixed into the stochastic rounding of 16-bit storage
-  int round_nearest;        // 16-bit storage: round to nearest instead of stochastically
   // FP32 copies of the double scalars above (set_fp32_copies), read by the FP32-compute kernels
   float force_f[3], omega_f, rho_l_f, drho_f, nu_l_f, dnu_f;
 };
@@ -91,14 +90,13 @@ __device__ __forceinline__ T ld_field(const S* base, long long idx, float dec) {
 
 // one field of a time step's output: 16-bit storage is scaled and rounded stochastically with the
 // next word of the site's random sequence rs
-template <class S, class T>
-__device__ __forceinline__ void st_field(S* base, long long idx, T v, float enc, uint32_t& rs, bool nearest) {
-  if constexpr (Codec<S>::scaled) {
+template <class S, bool NEAREST, class T>
+__device__ __forceinline__ void st_field(S* base, long long idx, T v, float enc, uint32_t& rs) {
+  if constexpr (Codec<S>::scaled && NEAREST) {
+    Codec<S>::store(base + idx, static_cast<float>(v) * enc);
+  } else if constexpr (Codec<S>::scaled) {
     rs = lcg_next(rs);
-    if (nearest)
-      Codec<S>::store(base + idx, static_cast<float>(v) * enc);
-    else
-      Codec<S>::store_sr(base + idx, static_cast<float>(v) * enc, rs);
+    Codec<S>::store_sr(base + idx, static_cast<float>(v) * enc, rs);
   } else {
     Codec<S>::store(base + idx, v);
   }
@@ -261,7 +259,11 @@ struct TmaBox {
   static constexpr int A = 16 / int(sizeof(S));
   static constexpr int BX = ((32 + A - 1) + A - 1) / A * A;
 };
-constexpr int kRawStages = 2;  // plane patches in flight per CTA
+// plane patches in flight per CTA (TMA stages)
+#ifndef LBF_RAW_STAGES
+#define LBF_RAW_STAGES 2
+#endif
+constexpr int kRawStages = LBF_RAW_STAGES;
 
 // a TMA destination in shared memory must start on a 128-byte boundary: every stage of the raw
 // ring is padded to a multiple of 128 bytes and the ring itself is aligned inside the dynamic
@@ -337,7 +339,7 @@ constexpr int fwd_minb(int Q, int bytes) {
 
 constexpr uint32_t kWaitPolls = 1u << 20;  // bound of every mbarrier wait
 
-template <class L, class S, int BY, bool MASK, bool TWO, bool FF, bool TMA>
+template <class L, class S, int BY, bool MASK, bool TWO, bool FF, bool TMA, bool RN>
 __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeof(S))))
     k_stream_collide(const FwdParams a, const __grid_constant__ CUtensorMap tmap) {
   using T = typename ComputeOf<S>::type;
@@ -358,7 +360,6 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   constexpr bool SITEF = TWO || FF;  // per-site force (else the uniform force of the parameters)
   static_assert(fwd_smem_bytes<L, S, BY, MASK, TMA>() >= 6 * 512 * sizeof(double), "smem too small for the final tree");
   static_assert(FwdTile<BY>::THREADS <= 512, "final tree assumes <= 512 threads");
-  static_assert(kRawStages == 2, "plane parities below assume two raw stages");
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   S* rawst = reinterpret_cast<S*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   int issued = pbase - 1;  // last plane whose TMA load was issued (elected thread)
   auto issue = [&](int p) {  // elected thread only
     if (p > z1 || abort_flag) return;
-    const int s = (p - pbase) & 1;
+    const int s = (p - pbase) % kRawStages;
     S* dstp = rawst + s * STAGE_STRIDE;
     if ((smem_u32(dstp) & 127u) != 0u) {  // never issue a copy the hardware would reject
       atomicOr(a.flags, 4u);
@@ -417,8 +418,8 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   };
   auto wait_plane = [&](int p) {
     if (abort_flag) return;
-    const int s = (p - pbase) & 1;
-    const uint32_t parity = uint32_t((p - pbase) >> 1) & 1u;
+    const int s = (p - pbase) % kRawStages;
+    const uint32_t parity = uint32_t((p - pbase) / kRawStages) & 1u;
     if (!mbar_wait_bounded(&bars[s], parity, kWaitPolls)) {
       atomicOr(a.flags, 2u);
       abort_flag = 1;
@@ -498,7 +499,8 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   auto stage = [&](auto par_c, int p, int g2, const SiteExtra<T, TWO>& e) -> bool {
     constexpr int par = decltype(par_c)::value;
     T m[10];
-    read_raw(p, par, m);
+    // raw stage of plane p: (p - pbase) mod kRawStages, the plane parity when there are two
+    read_raw(p, kRawStages == 2 ? par : (p - pbase) % kRawStages, m);
     T inv2rho = T(0.5), omm = one_m_omega;
     if constexpr (TWO) {
       // equal densities (the only two-component case built): 1/(2 rho) is a constant; the
@@ -699,18 +701,20 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
       if (outcol && !sol_0) {
         const long long zc = (long long)z * plane + col;
         // random sequence of this site and step (16-bit storage only)
-        uint32_t rs = Codec<S>::scaled ? fmix32(uint32_t(zc) ^ a.salt) : 0u;
-        const bool rn = a.round_nearest != 0;
-        st_field<S, T>(dst, zc, A.a0, a.sc.enc[0], rs, rn);
-        st_field<S, T>(dst + N, zc, ux, a.sc.enc[1], rs, rn);
-        st_field<S, T>(dst + 2 * N, zc, uy, a.sc.enc[1], rs, rn);
-        st_field<S, T>(dst + 3 * N, zc, uz, a.sc.enc[1], rs, rn);
-        st_field<S, T>(dst + 4 * N, zc, nxx, a.sc.enc[2], rs, rn);
-        st_field<S, T>(dst + 5 * N, zc, nyy, a.sc.enc[2], rs, rn);
-        st_field<S, T>(dst + 6 * N, zc, nzz, a.sc.enc[2], rs, rn);
-        st_field<S, T>(dst + 7 * N, zc, nxy, a.sc.enc[2], rs, rn);
-        st_field<S, T>(dst + 8 * N, zc, nxz, a.sc.enc[2], rs, rn);
-        st_field<S, T>(dst + 9 * N, zc, nyz, a.sc.enc[2], rs, rn);
+        {
+          // 16-bit storage rounds stochastically unless RN (round to nearest); FP32/FP64 stores are plain
+          uint32_t rs = Codec<S>::scaled && !RN ? fmix32(uint32_t(zc) ^ a.salt) : 0u;
+          st_field<S, RN>(dst, zc, A.a0, a.sc.enc[0], rs);
+          st_field<S, RN>(dst + N, zc, ux, a.sc.enc[1], rs);
+          st_field<S, RN>(dst + 2 * N, zc, uy, a.sc.enc[1], rs);
+          st_field<S, RN>(dst + 3 * N, zc, uz, a.sc.enc[1], rs);
+          st_field<S, RN>(dst + 4 * N, zc, nxx, a.sc.enc[2], rs);
+          st_field<S, RN>(dst + 5 * N, zc, nyy, a.sc.enc[2], rs);
+          st_field<S, RN>(dst + 6 * N, zc, nzz, a.sc.enc[2], rs);
+          st_field<S, RN>(dst + 7 * N, zc, nxy, a.sc.enc[2], rs);
+          st_field<S, RN>(dst + 8 * N, zc, nxz, a.sc.enc[2], rs);
+          st_field<S, RN>(dst + 9 * N, zc, nyz, a.sc.enc[2], rs);
+        }
         if (!(uu <= T(a.umax2))) atomicOr(a.flags, 1u);
         red[0] += A.a0;
         red[1] += ux;
@@ -752,8 +756,8 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     // after an aborted wait, let the copies still in flight land before the CTA exits (bounded)
     if (abort_flag && me == 0) {
       for (int p = max(pbase, issued - kRawStages + 1); p <= issued; ++p) {
-        const int s = (p - pbase) & 1;
-        mbar_wait_bounded(&bars[s], uint32_t((p - pbase) >> 1) & 1u, kWaitPolls);
+        const int s = (p - pbase) % kRawStages;
+        mbar_wait_bounded(&bars[s], uint32_t((p - pbase) / kRawStages) & 1u, kWaitPolls);
       }
     }
   }
