@@ -9,16 +9,21 @@
 //   * a CTA owns an x-y tile of 30 x BY output columns and marches along z through a chunk of planes;
 //   * it has BY+2 warps; warp r holds one row of 32 consecutive sites: the 30 outputs of that row
 //     plus the x halo on either side (lanes 0 and 31), and warps 0 and BY+1 are the y halo rows;
-//   * per plane every thread loads its site's 10 stored values (coalesced SoA loads), forms the
-//     post-collision Hermite coefficients P and the Q populations f_q = w_q [P0 + 3 c.P1 +
-//     (9/2) (c c - delta/3) : P2] and writes them to slot (z+1) of a 3-plane ring;
-//   * after a barrier the output threads pull f_q(x - c_q) from the ring (planes z-1, z, z+1),
-//     sum them pairwise into the new moments, apply the half-force correction and store.
+//   * per plane one elected thread loads the 10 stored fields of the whole patch with a TMA box
+//     into a two-stage shared-memory buffer (the y-halo warps wait for it, see below); every thread
+//     forms the post-collision Hermite coefficients P of its site and the Q populations
+//     f_q / w_q = P0 + 3 c.P1 + (9/2) (c c - delta/3) : P2 and writes them to a ring split by c_z
+//     (the axial directions stay in registers);
+//   * after a barrier the output threads pull f_q(x - c_q) from planes z-1, z, z+1, sum them
+//     pairwise with the weights w_q into the new moments, apply the half-force correction and
+//     store;
+//   * during the outputs the idle y-halo warps wait for the next plane's TMA box, so the next
+//     iteration starts without any thread polling the mbarrier.
 // Halfway bounce-back: where x - c_q is solid the pulled value is the opposite population of x
 // itself. A block-wide OR of the solid flags of the three ring planes skips that logic for tiles
 // with no wall nearby.
-// The conservation sums (sum p*, sum u, sum phi, sum u.u) are accumulated per thread and reduced
-// in FP64 across the CTA into one partial per block (deterministic second stage elsewhere).
+// The conservation sums (sum p*, sum u, sum phi, sum u.u) are accumulated per thread, reduced in
+// FP64 across the CTA into one partial per block, and summed in a fixed order by the last block.
 #pragma once
 
 #include "lattice.cuh"
