@@ -124,13 +124,15 @@ class ClockSampler:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3].split()[0]) for r in rows if r[3].split() and r[3].split()[0].replace(".", "").isdigit()]
         reasons = set()
         for r in rows:
             for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w": statistics.median(pw) if pw else None}
 
 
 def gpu_identifier(torch, dev):
@@ -343,6 +345,14 @@ def extras(torch, device, quick):
     return out
 
 
+def energy_per_update(clocks, seconds_per_step, sites):
+    """nJ per lattice update from the median board power sampled during the timed steps."""
+    if not clocks or clocks.get("power_w") is None:
+        return None
+    return {"nJ_per_lup": round(clocks["power_w"] * seconds_per_step / sites * 1e9, 4), "power_w": clocks["power_w"],
+            "source": "nvidia-smi power.draw, median over the timed region"}
+
+
 def max_over_ranks(torch, dist, t, device):
     """The job's time: the slowest rank's (every rank gets it)."""
     tt = torch.tensor([t], dtype=torch.float64, device=device)
@@ -424,6 +434,9 @@ def run_ours(args):
                      "bytes_per_lup": bpl, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
         "gpu_launches": args.steps,
         "clocks": clocks,
+        # board power (median of the samples in the timed region) x time per step / sites: the
+        # energy per lattice update the paper reports for its weak-scaling runs
+        "energy": energy_per_update(clocks, t / args.steps, n),
         "sums_after": {"sum_p": sums[0], "sum_ux": sums[1]},
     }
     if world == 1 and not args.kernel_only and args.workload == "channel256":

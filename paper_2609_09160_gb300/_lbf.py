@@ -5,7 +5,8 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "liblbf.so")
+# LBF_LIBRARY selects another build of the same library (e.g. the index-checked liblbf_debug.so)
+LIB_PATH = os.environ.get("LBF_LIBRARY") or os.path.join(_PKG, "liblbf.so")
 
 LBF_D3Q19, LBF_D3Q27 = 19, 27
 LBF_F64, LBF_F32, LBF_F16, LBF_BF16 = 0, 1, 2, 3

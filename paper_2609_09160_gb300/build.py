@@ -38,14 +38,17 @@ def _inputs():
 
 
 STAMP = os.path.join(BUILD, "flags.txt")
+# index-checked variant (LBF_DEBUG): its own objects and library, never loaded by default
+DEBUG_BUILD = os.path.join(PKG, "_build_debug")
+DEBUG_LIB = os.path.join(PKG, "liblbf_debug.so")
 
 
-def up_to_date(tuning=()):
-    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+def up_to_date(tuning=(), lib=LIB, stamp=STAMP):
+    if not os.path.exists(lib) or not os.path.exists(stamp):
         return False
-    if open(STAMP).read() != " ".join(tuning):
+    if open(stamp).read() != " ".join(tuning):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
@@ -62,10 +65,10 @@ def _units():
     return units
 
 
-def _compile(unit, extra):
+def _compile(unit, extra, build_dir=BUILD):
     src, name, defines = unit
-    obj = os.path.join(BUILD, name + ".o")
-    log = os.path.join(BUILD, name + ".log")
+    obj = os.path.join(build_dir, name + ".o")
+    log = os.path.join(build_dir, name + ".log")
     cmd = [nvcc()] + NVCC_FLAGS + defines + extra + ["-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     with open(log, "w") as f:
@@ -75,27 +78,31 @@ def _compile(unit, extra):
     return obj
 
 
-def build(force=False, verbose_ptxas=False):
+def build(force=False, verbose_ptxas=False, debug=False):
     """Compile liblbf.so in place; returns its path. LBF_NVCC_EXTRA (space-separated nvcc flags,
-    e.g. tile-size defines) is appended for tuning builds and forces a rebuild."""
+    e.g. tile-size defines) is appended for tuning builds and forces a rebuild. debug=True builds
+    liblbf_debug.so instead: the same library with every index of the fused step checked
+    (LBF_DEBUG), for tests; load it by pointing LBF_LIBRARY at it."""
     tuning = os.environ.get("LBF_NVCC_EXTRA", "").split()
-    if not force and up_to_date(tuning):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + tuning
+    build_dir, lib = (DEBUG_BUILD, DEBUG_LIB) if debug else (BUILD, LIB)
+    stamp = os.path.join(build_dir, "flags.txt")
+    if not force and up_to_date(tuning, lib, stamp):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + tuning + (["-DLBF_DEBUG"] if debug else [])
     units = _units()
     workers = max(1, min(len(units), os.cpu_count() or 1))
     with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
-        objs = list(ex.map(lambda u: _compile(u, extra), units))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda u: _compile(u, extra, build_dir), units))
+    tmp = lib + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr[-4000:]}")
-    os.replace(tmp, LIB)
-    with open(STAMP, "w") as f:
+    os.replace(tmp, lib)
+    with open(stamp, "w") as f:
         f.write(" ".join(tuning))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

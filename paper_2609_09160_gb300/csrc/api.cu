@@ -772,6 +772,7 @@ lbf_status lbf_synchronize(lbf_ctx* c) {
   unsigned f = 0;
   LBF_CUDA(cudaMemcpyAsync(&f, c->flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
   LBF_CUDA(cudaStreamSynchronize(c->stream));
+  if (f & 8u) return fail(LBF_EINTERNAL, "an index check of the LBF_DEBUG build failed");
   if (f & 6u) return fail(LBF_EINTERNAL, (f & 4u) ? "a TMA stage was misaligned; the step was abandoned"
                                                   : "a TMA plane load did not complete in time; the step was abandoned");
   if (f & 1u) c->unstable_seen = true;

@@ -344,6 +344,20 @@ constexpr int fwd_minb(int Q, int bytes) {
 
 constexpr uint32_t kWaitPolls = 1u << 20;  // bound of every mbarrier wait
 
+// LBF_DEBUG builds check every shared-memory and global index of the step against the buffer it
+// addresses; a failed check sets bit 3 of the error flags (reported as LBF_EINTERNAL) and never
+// traps. Release builds compile the checks away.
+#ifdef LBF_DEBUG
+#define LBF_CHECK(flags, cond)        \
+  do {                                \
+    if (!(cond)) atomicOr(flags, 8u); \
+  } while (0)
+#else
+#define LBF_CHECK(flags, cond) \
+  do {                         \
+  } while (0)
+#endif
+
 template <class L, class S, int BY, bool MASK, bool TWO, bool FF, bool TMA, bool RN>
 __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeof(S))))
     k_stream_collide(const FwdParams a, const __grid_constant__ CUtensorMap tmap) {
@@ -417,6 +431,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     }
     // no proxy fence: the stage is only read through the generic proxy, and every read of it
     // completed before the barrier that precedes this call
+    LBF_CHECK(a.flags, (xa * int(sizeof(S))) % 16 == 0 && s >= 0 && s < kRawStages);
     mbar_arrive_expect_tx(&bars[s], uint32_t(STAGE_ELEMS * sizeof(S)));
     tma_load_4d(dstp, &tmap, &bars[s], xa, int(blockIdx.y) * BY - 1, wrap(p, a.nz), 0);
     issued = p;
@@ -463,6 +478,8 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   auto read_raw = [&](int p, int st, T (&m)[10]) {
     if (TMA && inbox) {
       const S* b = raw_me + st * STAGE_STRIDE;
+      LBF_CHECK(a.flags, st >= 0 && st < kRawStages && lane + xoff < BX &&
+                             (b - rawst) + 9 * ROWS * BX < kRawStages * STAGE_STRIDE);
 #pragma unroll
       for (int k = 0; k < 10; ++k) {
         const float dec = k == 0 ? a.sc.dec[0] : (k < 4 ? a.sc.dec[1] : a.sc.dec[2]);
@@ -539,6 +556,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
       } else {
         constexpr int g = D::group(q);
         T* b = g == 0 ? w0 : (g == 1 ? w1 : w2);
+        LBF_CHECK(a.flags, (b + D::gidx(q) * SITES) - ring >= 0 && (b + D::gidx(q) * SITES) - ring < R::VALUES);
         b[D::gidx(q) * SITES] = v;
       }
     };
@@ -653,9 +671,12 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
           constexpr int cx = L::cx(q), cy = L::cy(q), cz = L::cz(q);
           constexpr int g = D::group(q);
           constexpr int off = D::gidx(q) * SITES - cy * 32 - cx;
+          LBF_CHECK(a.flags, ((g == 0 ? P0 : (g == 1 ? P1 : P2)) + off) - ring >= -kRingPad &&
+                                 ((g == 0 ? P0 : (g == 1 ? P1 : P2)) + off) - ring < R::VALUES + kRingPad);
           T v = (g == 0 ? P0 : (g == 1 ? P1 : P2))[off];
           if constexpr (W) {
             const uint8_t* mk = cz > 0 ? MM : (cz < 0 ? MP : M0);
+            LBF_CHECK(a.flags, (mk - cy * 32 - cx) - msk >= -kRingPad && (mk - cy * 32 - cx) - msk < 3 * SITES + kRingPad);
             if (mk[-cy * 32 - cx]) {  // halfway bounce-back: own post-collision population of opp(q)
               constexpr int o = L::opp(q);
               constexpr int go = D::group(o);
@@ -705,6 +726,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
       const T uu = ux * ux + uy * uy + uz * uz;
       if (outcol && !sol_0) {
         const long long zc = (long long)z * plane + col;
+        LBF_CHECK(a.flags, z >= 0 && z < a.nz && col >= 0 && col < plane && zc + 9 * N < 10 * N);
         // random sequence of this site and step (16-bit storage only)
         {
           // 16-bit storage rounds stochastically unless RN (round to nearest); FP32/FP64 stores are plain
