@@ -216,12 +216,13 @@ def adjoint_rollout(torch, device, T=500, K=50, reps=2):
     return times[-1], s.N
 
 
-def channel_solver(torch, device, storage="f32", lattice=19, shape=SHAPE):
+def channel_solver(torch, device, storage="f32", lattice=19, shape=SHAPE, populations=False):
     import synth
     from paper_2609_09160_gb300 import Solver
 
     M0, solid = synth.channel(shape, 1e-3, seed=1, dtype=torch.float32)
-    s = Solver(shape, lattice=lattice, tau=0.9, storage=storage, force=(1e-6, 0.0, 0.0), mask=solid, device=device)
+    s = Solver(shape, lattice=lattice, tau=0.9, storage=storage, force=(1e-6, 0.0, 0.0), mask=solid, device=device,
+               populations=populations)
     return s, M0, solid
 
 
@@ -320,6 +321,16 @@ def extras(torch, device, quick):
             del s
             torch.cuda.empty_cache()
     del M0
+    torch.cuda.empty_cache()
+
+    # the same channel in the population representation (Q = 19 FP32 fields per buffer, 152 B + mask
+    # per update): the layout the paper's moment representation replaces
+    s, M0, _ = channel_solver(torch, device, populations=True)
+    s.set_moments(M0.to(device))
+    r = rate(s, 50 if quick else 200, 5, 2 * 19 * 4 + 1)
+    r["note"] = "population-form reference kernel (lbf_params.populations), same scheme and workload as the headline"
+    out["channel256_d3q19_f32_populations"] = r
+    del s, M0
     torch.cuda.empty_cache()
 
     # two-component droplet, 128^3, R = 20, equal densities, tau = 1 (config of the Laplace test)

@@ -91,6 +91,14 @@ typedef struct {
   void* stream;         /* cudaStream_t used for every call; NULL = legacy default stream */
   int rounding;         /* LBF_ROUND_STOCHASTIC (0, default) or LBF_ROUND_NEAREST: 16-bit stores of
                            a time step; ignored for FP32/FP64 storage */
+  int populations;      /* nonzero: population-form reference representation - the context stores
+                           the Q populations f(x, t) of Eq. (pullLB) after streaming instead of
+                           the 10 moments (the memory layout the paper compares against, Sec. 3)
+                           and steps them with the same regularized collision (collide, then push
+                           with halfway bounce-back). Every call keeps its meaning (moments in,
+                           moments out); state buffers hold Q fields; the sums of lbf_reduce are
+                           computed from the state when asked. FP32/FP64 storage, single
+                           component, no adjoint (LBF_ENOTSUP). */
 } lbf_params;
 
 /* Workspace bytes the context needs for these parameters, 0 if the parameters are invalid.

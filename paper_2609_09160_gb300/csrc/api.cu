@@ -58,7 +58,7 @@ size_t storage_bytes(int storage) {
 size_t compute_bytes(int storage) { return storage == LBF_F64 ? 8 : 4; }
 
 struct Layout {
-  size_t state[2], mask, phi[2], F[2], G, partials, scal, staging, total;
+  size_t state[2], mom, mask, phi[2], F[2], G, partials, scal, staging, total;
   long long npartials;
   size_t staging_bytes;
 };
@@ -72,6 +72,12 @@ lbf_status check_params(const lbf_params* p) {
   if (storage_bytes(p->storage) == 0) return fail(LBF_EINVAL, "storage must be LBF_F64, LBF_F32, LBF_F16 or LBF_BF16");
   if (p->rounding != LBF_ROUND_STOCHASTIC && p->rounding != LBF_ROUND_NEAREST)
     return fail(LBF_EINVAL, "rounding must be LBF_ROUND_STOCHASTIC or LBF_ROUND_NEAREST");
+  if (p->populations && (p->storage == LBF_F16 || p->storage == LBF_BF16))
+    return fail(LBF_ENOTSUP, "the population representation needs LBF_F32 or LBF_F64 storage");
+  if (p->populations && p->two_component)
+    return fail(LBF_ENOTSUP, "the population representation is single-component only");
+  if (p->populations && (p->ny > 65535 || p->nz > 65535))
+    return fail(LBF_ENOTSUP, "the population representation launches one block row per (y, z): ny, nz <= 65535");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(p->force[a])) return fail(LBF_EINVAL, "force must be finite");
   if (p->two_component) {
@@ -105,8 +111,12 @@ bool make_layout(const lbf_params* p, Layout* L) {
     off = align_up(off + bytes);
     return at;
   };
-  L->state[0] = take(10 * N * sb);
-  L->state[1] = take(10 * N * sb);
+  // state buffers: 10 moment fields, or Q population fields in the population representation
+  // (which also keeps one 10-field moment buffer: read-out target and the solid sites' moments)
+  const long long fields = p->populations ? p->lattice : 10;
+  L->state[0] = take(fields * N * sb);
+  L->state[1] = take(fields * N * sb);
+  L->mom = p->populations ? take(10 * N * sb) : 0;
   L->mask = p->mask ? take(N) : 0;
   if (p->two_component) {
     L->phi[0] = take(N * cb);
@@ -171,6 +181,10 @@ struct lbf_ctx {
   bool unstable_seen;
   double omega, nu_l, nu_h;
   unsigned long long steps_done;  // forward launches so far: selects the rounding words of a step
+  bool pops;                      // population representation (state buffers hold Q fields)
+  PopKernels popk;
+  void* mom;                      // pops: internal moment state (read-out target, solid sites kept)
+  dim3 pop_grid;                  // pops: (ceil(nx / 256), ny, nz) blocks of 256 threads
 };
 
 namespace {
@@ -363,6 +377,38 @@ FwdParams forward_params(const lbf_ctx* c, const void* src, void* dst, bool redu
   return a;
 }
 
+PopParams pop_params(const lbf_ctx* c, const void* src, void* dst, bool reduce) {
+  PopParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.src = src;
+  p.dst = dst;
+  p.mom = c->mom;
+  p.mask = c->mask_d;
+  p.force_field = c->prm.force_field;
+  for (int k = 0; k < 3; ++k) {
+    p.force[k] = c->prm.force[k];
+    p.force_f[k] = float(c->prm.force[k]);
+  }
+  p.omega = c->omega;
+  p.omega_f = float(c->omega);
+  p.nx = c->nx;
+  p.ny = c->ny;
+  p.nz = c->nz;
+  p.N = c->N;
+  (void)reduce;  // the population step does not fuse the sums: lbf_reduce takes them from the state
+  p.flags = c->flags;
+  p.umax2 = 0.16f;
+  return p;
+}
+
+// population representation: the internal moments of the current state into c->mom
+lbf_status pop_moments(lbf_ctx* c) {
+  PopParams pp = pop_params(c, c->state[c->cur], nullptr, false);
+  void* args[] = {&pp};
+  LBF_CUDA(cudaLaunchKernel(c->popk.moments, c->pop_grid, dim3(kPopThreads), args, 0, c->stream));
+  return LBF_OK;
+}
+
 lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out) {
   CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   switch (c->storage) {
@@ -384,6 +430,12 @@ lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out
 }
 
 lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
+  if (c->pops) {
+    PopParams pp = pop_params(c, src, dst, reduce);
+    void* args[] = {&pp};
+    LBF_CUDA(cudaLaunchKernel(c->popk.step, c->pop_grid, dim3(kPopThreads), args, 0, c->stream));
+    return LBF_OK;
+  }
   FwdParams a = forward_params(c, src, dst, reduce);
   ++c->steps_done;
   CUtensorMap tm;
@@ -414,12 +466,17 @@ lbf_status finalize_sums(lbf_ctx* c, long long nblocks) {
 
 template <class S>
 void launch_reduce_state_T(lbf_ctx* c, unsigned grid) {
-  k_reduce_state<S><<<grid, 256, 0, c->stream>>>(static_cast<const S*>(c->state[c->cur]), c->N, c->mask_d,
+  const void* st = c->pops ? c->mom : c->state[c->cur];
+  k_reduce_state<S><<<grid, 256, 0, c->stream>>>(static_cast<const S*>(st), c->N, c->mask_d,
                                                    c->two ? c->phi[c->pcur] : nullptr, c->storage == LBF_F64, c->sc,
                                                    c->partials);
 }
 
 lbf_status reduce_state(lbf_ctx* c) {
+  if (c->pops) {
+    const lbf_status st = pop_moments(c);
+    if (st != LBF_OK) return st;
+  }
   const unsigned grid = (unsigned)std::min<long long>(1024, std::max<long long>(1, (c->N + 255) / 256));
   switch (c->storage) {
     case LBF_F64: launch_reduce_state_T<double>(c, grid); break;
@@ -517,6 +574,9 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   c->state[0] = c->ws + L.state[0];
   c->state[1] = c->ws + L.state[1];
   c->cur = 0;
+  c->pops = params->populations != 0;
+  c->mom = c->pops ? c->ws + L.mom : nullptr;
+  c->pop_grid = dim3((c->nx + kPopThreads - 1) / kPopThreads, c->ny, c->nz);
   c->mask_d = c->has_mask ? reinterpret_cast<uint8_t*>(c->ws + L.mask) : nullptr;
   for (int k = 0; k < 2; ++k) {
     c->phi[k] = c->two ? c->ws + L.phi[k] : nullptr;
@@ -543,6 +603,12 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   c->tma = tma_eligible(c->storage, c->nx);
   c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two, params->force_field != nullptr, c->tma,
                        params->rounding == LBF_ROUND_NEAREST);
+  c->popk = c->pops ? pop_kernels_for(c->Q, c->storage, c->has_mask, params->force_field != nullptr)
+                    : PopKernels{nullptr, nullptr, nullptr};
+  if (c->pops && c->popk.step == nullptr) {
+    delete c;
+    return fail(LBF_ENOTSUP, "no population kernel for this combination");
+  }
   c->adj = adjoint_for(c->Q, c->storage, c->has_mask);
   if (c->fwd.fn == nullptr) {
     delete c;
@@ -622,7 +688,9 @@ lbf_status lbf_destroy(lbf_ctx* c) {
   return LBF_OK;
 }
 
-size_t lbf_state_bytes(const lbf_ctx* c) { return c ? size_t(10) * c->N * storage_bytes(c->storage) : 0; }
+size_t lbf_state_bytes(const lbf_ctx* c) {
+  return c ? size_t(c->pops ? c->Q : 10) * c->N * storage_bytes(c->storage) : 0;
+}
 
 lbf_status lbf_set_moments(lbf_ctx* c, const void* src, int dt, const void* phi) {
   if (c == nullptr || src == nullptr) return fail(LBF_EINVAL, "NULL argument");
@@ -656,9 +724,10 @@ lbf_status lbf_set_moments(lbf_ctx* c, const void* src, int dt, const void* phi)
     }
     set_scales(c, m);
   }
+  void* enc_dst = c->pops ? c->mom : c->state[0];  // populations are built from the moments below
   if (dev) {
-    if (dt == LBF_F64) encode_dispatch<double>(c->storage, src, N, 0, N, c->state[0], N, c->sc, s);
-    else encode_dispatch<float>(c->storage, src, N, 0, N, c->state[0], N, c->sc, s);
+    if (dt == LBF_F64) encode_dispatch<double>(c->storage, src, N, 0, N, enc_dst, N, c->sc, s);
+    else encode_dispatch<float>(c->storage, src, N, 0, N, enc_dst, N, c->sc, s);
     LBF_CUDA(cudaGetLastError());
   } else {
     const long long chunk = std::max<long long>(1, (long long)(c->lay.staging_bytes / (10 * eb)));
@@ -667,10 +736,15 @@ lbf_status lbf_set_moments(lbf_ctx* c, const void* src, int dt, const void* phi)
       const long long cnt = std::min(chunk, N - s0);
       for (int k = 0; k < 10; ++k)
         LBF_CUDA(cudaMemcpyAsync(c->staging + k * cnt * eb, h + (k * N + s0) * eb, cnt * eb, cudaMemcpyHostToDevice, s));
-      if (dt == LBF_F64) encode_dispatch<double>(c->storage, c->staging, cnt, s0, cnt, c->state[0], N, c->sc, s);
-      else encode_dispatch<float>(c->storage, c->staging, cnt, s0, cnt, c->state[0], N, c->sc, s);
+      if (dt == LBF_F64) encode_dispatch<double>(c->storage, c->staging, cnt, s0, cnt, enc_dst, N, c->sc, s);
+      else encode_dispatch<float>(c->storage, c->staging, cnt, s0, cnt, enc_dst, N, c->sc, s);
       LBF_CUDA(cudaGetLastError());
     }
+  }
+  if (c->pops) {
+    PopParams pp = pop_params(c, nullptr, c->state[0], false);
+    void* args[] = {&pp};
+    LBF_CUDA(cudaLaunchKernel(c->popk.init, c->pop_grid, dim3(kPopThreads), args, 0, s));
   }
   LBF_CUDA(cudaMemcpyAsync(c->state[1], c->state[0], lbf_state_bytes(c), cudaMemcpyDeviceToDevice, s));
   c->cur = 0;
@@ -714,7 +788,7 @@ lbf_status lbf_step(lbf_ctx* c, int n) {
     c->cur ^= 1;
     if (c->two) c->pcur ^= 1;
   }
-  if (n > 0) c->sums_valid = true;  // the last step's kernel wrote them
+  if (n > 0) c->sums_valid = !c->pops;  // the last moment step's kernel wrote them
   return c->unstable_seen ? fail(LBF_EUNSTABLE, "instability flagged by an earlier step") : LBF_OK;
 }
 
@@ -731,6 +805,11 @@ lbf_status lbf_moments(lbf_ctx* c, void* dst, int dt, void* phi_dst) {
   const size_t eb = dt == LBF_F64 ? 8 : 4;
   cudaStream_t s = c->stream;
   const void* st = c->state[c->cur];
+  if (c->pops) {
+    const lbf_status ps = pop_moments(c);
+    if (ps != LBF_OK) return ps;
+    st = c->mom;
+  }
   if (is_device_pointer(dst)) {
     if (dt == LBF_F64) decode_dispatch<double>(c->storage, st, N, 0, N, dst, N, c->sc, s);
     else decode_dispatch<float>(c->storage, st, N, 0, N, dst, N, c->sc, s);
@@ -812,6 +891,7 @@ lbf_status lbf_adjoint_step(lbf_ctx* c, const void* state_t, const void* state_t
       grad_force == nullptr || lambda_in == lambda_out)
     return fail(LBF_EINVAL, "bad argument");
   if (c->two) return fail(LBF_ENOTSUP, "the adjoint is single-component only");
+  if (c->pops) return fail(LBF_ENOTSUP, "the adjoint works on the moment representation");
   if (c->adj.fn == nullptr) return fail(LBF_ENOTSUP, "the adjoint needs LBF_F32 or LBF_F64 storage");
   AdjParams a;
   std::memset(&a, 0, sizeof(a));

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "adjoint.cuh"
+#include "population.cuh"
 #include "stream_collide.cuh"
 
 namespace lbf {
@@ -69,9 +70,36 @@ KernelInfo forward_kernel_ls(bool mask, bool two, bool field, bool tma, bool nea
              : forward_kernel_s<L, S, false, false>(mask, two, field);
 }
 
+// population-form reference kernels of lattice L, storage S (FP32/FP64 only; nulls otherwise)
+struct PopKernels {
+  const void* step;     // k_pop_step
+  const void* init;     // k_pop_from_moments
+  const void* moments;  // k_pop_moments
+};
+
+template <class L, class T, bool MASK, bool FF>
+PopKernels pop_kernels_info() {
+  return PopKernels{reinterpret_cast<const void*>(&k_pop_step<L, T, MASK, FF>),
+                    reinterpret_cast<const void*>(&k_pop_from_moments<L, T, FF>),
+                    reinterpret_cast<const void*>(&k_pop_moments<L, T, MASK, FF>)};
+}
+
+template <class L, class S>
+PopKernels pop_kernels_ls(bool mask, bool field) {
+  if constexpr (std::is_same<S, float>::value || std::is_same<S, double>::value) {
+    if (mask) return field ? pop_kernels_info<L, S, true, true>() : pop_kernels_info<L, S, true, false>();
+    return field ? pop_kernels_info<L, S, false, true>() : pop_kernels_info<L, S, false, false>();
+  } else {
+    (void)mask;
+    (void)field;
+    return PopKernels{nullptr, nullptr, nullptr};
+  }
+}
+
 // entry points implemented per (lattice, storage) translation unit
 #define LBF_DECLARE_TU(q, s)                                                             \
   KernelInfo forward_kernel_q##q##_s##s(bool mask, bool two, bool field, bool tma, bool nearest); \
+  PopKernels pop_kernels_q##q##_s##s(bool mask, bool field);                                        \
   KernelInfo adjoint_kernel_q##q##_s##s(bool mask);
 LBF_DECLARE_TU(19, 0)
 LBF_DECLARE_TU(19, 1)
@@ -97,6 +125,15 @@ inline KernelInfo forward_kernel_for(int lattice, int storage, bool mask, bool t
       return q19 ? forward_kernel_q19_s3(mask, two, field, tma, nearest) : forward_kernel_q27_s3(mask, two, field, tma, nearest);
   }
   return KernelInfo{nullptr, 0, 0, 0, 0};
+}
+
+inline PopKernels pop_kernels_for(int lattice, int storage, bool mask, bool field) {
+  const bool q19 = lattice == 19;
+  switch (storage) {
+    case ST_F64: return q19 ? pop_kernels_q19_s0(mask, field) : pop_kernels_q27_s0(mask, field);
+    case ST_F32: return q19 ? pop_kernels_q19_s1(mask, field) : pop_kernels_q27_s1(mask, field);
+  }
+  return PopKernels{nullptr, nullptr, nullptr};
 }
 
 // adjoint kernel (FP64 and FP32 storage only; fn == nullptr otherwise)

@@ -37,6 +37,10 @@ KernelInfo LBF_CAT(forward_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool ma
   return forward_kernel_ls<TuL, TuS>(mask, two, field, tma, nearest);
 }
 
+PopKernels LBF_CAT(pop_kernels_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask, bool field) {
+  return pop_kernels_ls<TuL, TuS>(mask, field);
+}
+
 KernelInfo LBF_CAT(adjoint_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask) {
 #if LBF_TU_STORAGE <= 1
   return mask ? adj_info<TuL, TuS, true>() : adj_info<TuL, TuS, false>();

@@ -97,6 +97,7 @@ extern "C" lbf_status lbf_step_static(const lbf_params* params, const void* src,
   lbf_status st = lbf_validate(params);
   if (st != LBF_OK) return st;
   if (params->two_component) return fail(LBF_ENOTSUP, "lbf_step_static is single-component only");
+  if (params->populations) return fail(LBF_ENOTSUP, "lbf_step_static works on the moment representation");
   if (params->storage != LBF_F32 && params->storage != LBF_F64)
     return fail(LBF_ENOTSUP, "lbf_step_static needs LBF_F32 or LBF_F64 storage (16-bit scales live in a context)");
   if (src == nullptr || dst == nullptr || src == dst) return fail(LBF_EINVAL, "src and dst must be distinct device buffers");

@@ -31,7 +31,8 @@ class Solver:
     """
 
     def __init__(self, shape, lattice=19, tau=0.8, storage="f32", force=(0.0, 0.0, 0.0), force_field=None,
-                 mask=None, two_component=None, scale_hint=None, rounding="stochastic", device=None):
+                 mask=None, two_component=None, scale_hint=None, rounding="stochastic", populations=False,
+                 device=None):
         nz, ny, nx = (int(v) for v in shape)
         self.shape = (nz, ny, nx)
         self.device = torch.device(device if device is not None else "cuda")
@@ -68,6 +69,7 @@ class Solver:
             for a in range(3):
                 p.scale_hint[a] = float(scale_hint[a])
         p.rounding = {"stochastic": _lbf.LBF_ROUND_STOCHASTIC, "nearest": _lbf.LBF_ROUND_NEAREST}[rounding]
+        p.populations = 1 if populations else 0
         with torch.cuda.device(self.device):
             self.stream = torch.cuda.current_stream(self.device)
             p.stream = self.stream.cuda_stream

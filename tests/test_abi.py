@@ -62,6 +62,17 @@ def params(**kw):
     return p
 
 
+def test_population_workspace_holds_two_population_buffers(lib):
+    """The population representation keeps Q fields per buffer (Sec. 3 memory model: 38 GB for
+    D3Q19 and 54 GB for D3Q27 in FP64 at 512^3 for the two buffers) plus one 10-field moment buffer."""
+    for lattice in (19, 27):
+        p = params(nx=512, ny=512, nz=512, storage=_lbf.LBF_F64, lattice=lattice, populations=1)
+        need = _lbf.lbf_workspace_bytes(p)
+        pops = 2 * lattice * 512 ** 3 * 8
+        assert pops + 10 * 512 ** 3 * 8 <= need < pops + 10 * 512 ** 3 * 8 + 64 * 2 ** 20
+        assert pops == {19: 38, 27: 54}[lattice] * 2 ** 30
+
+
 def test_workspace_holds_two_moment_buffers(lib):
     """Two buffers of 10 fields: the paper's 20 scalar fields per site (Sec. 3 memory model)."""
     for storage, b in ((_lbf.LBF_F64, 8), (_lbf.LBF_F32, 4), (_lbf.LBF_F16, 2), (_lbf.LBF_BF16, 2)):
@@ -79,6 +90,9 @@ def test_workspace_holds_two_moment_buffers(lib):
     (dict(tau=0.5), _lbf.LBF_EINVAL),
     (dict(storage=7), _lbf.LBF_EINVAL),
     (dict(rounding=2), _lbf.LBF_EINVAL),
+    (dict(populations=1, storage=_lbf.LBF_F16), _lbf.LBF_ENOTSUP),
+    (dict(populations=1, two_component=1, tau_l=1.0, tau_h=1.0, rho_l=1.0, rho_h=1.0, width=4.0, sigma=0.03,
+          diffusivity=0.1), _lbf.LBF_ENOTSUP),
     (dict(two_component=1, tau_l=1.0, tau_h=1.0, rho_l=0.5, rho_h=1.5, width=4.0, sigma=0.03, diffusivity=0.1),
      _lbf.LBF_ENOTSUP),
     (dict(two_component=1, tau_l=1.0, tau_h=0.4, rho_l=1.0, rho_h=1.0, width=4.0, sigma=0.03, diffusivity=0.1),
