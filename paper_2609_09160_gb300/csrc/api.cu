@@ -98,7 +98,7 @@ lbf_status check_params(const lbf_params* p) {
 
 int grid_x(int nx) { return (nx + FwdTile<8>::XOUT - 1) / FwdTile<8>::XOUT; }
 int grid_y(int ny, int by) { return (ny + by - 1) / by; }
-int fwd_by(int Q, int storage) { return fwd_rows(Q, int(storage_bytes(storage))); }
+int fwd_by(int Q, int storage, bool mask) { return fwd_rows(Q, int(storage_bytes(storage)), mask); }
 int min_zchunk(int nz) { return std::min(8, nz); }
 
 bool make_layout(const lbf_params* p, Layout* L) {
@@ -128,7 +128,7 @@ bool make_layout(const lbf_params* p, Layout* L) {
     L->phi[0] = L->phi[1] = L->F[0] = L->F[1] = L->G = 0;
   }
   const long long gz = (p->nz + min_zchunk(p->nz) - 1) / min_zchunk(p->nz);
-  L->npartials = std::max<long long>((long long)grid_x(p->nx) * grid_y(p->ny, fwd_by(p->lattice, p->storage)) * gz, 1024);
+  L->npartials = std::max<long long>((long long)grid_x(p->nx) * grid_y(p->ny, fwd_by(p->lattice, p->storage, p->mask != nullptr)) * gz, 1024);
   L->partials = take(size_t(L->npartials) * 8 * sizeof(double));
   L->scal = take(64 * sizeof(double));
   L->staging_bytes = std::min<size_t>(kStagingMax, size_t(11) * 8 * size_t(N));

@@ -246,11 +246,14 @@ struct Dirs {
   }
 };
 
-template <class L, int ROWS>
+// plane slots per group: c_z = -1 needs the plane being pulled (z+1) and, for bounce-back only,
+// the own plane z; c_z = 0 the pulled plane z and the one being staged; c_z = +1 the pulled plane
+// z-1, the plane z kept for the next output and the one being staged
+template <class L, int ROWS, bool MASK = true>
 struct GroupRing {
   using D = Dirs<L>;
   static constexpr int SITES = ROWS * 32;
-  static constexpr int NS0 = 2, NS1 = 2, NS2 = 3;
+  static constexpr int NS0 = MASK ? 2 : 1, NS1 = 2, NS2 = 3;
   __host__ __device__ static constexpr int base(int g) {
     return g == 0 ? 0 : (g == 1 ? NS0 * D::gsize(0) * SITES : (NS0 * D::gsize(0) + NS1 * D::gsize(1)) * SITES);
   }
@@ -286,7 +289,7 @@ template <class L, class S, int BY, bool MASK, bool TMA>
 constexpr size_t fwd_smem_bytes() {
   using T = typename ComputeOf<S>::type;
   const size_t raw = TMA ? 128 + size_t(kRawStages) * raw_stage_bytes<S, BY + 2>() : 0;
-  return raw + size_t(GroupRing<L, BY + 2>::VALUES + 2 * kRingPad) * sizeof(T) +
+  return raw + size_t(GroupRing<L, BY + 2, MASK>::VALUES + 2 * kRingPad) * sizeof(T) +
          (MASK ? size_t(3) * (BY + 2) * 32 + 2 * kRingPad : 0);
 }
 
@@ -331,15 +334,29 @@ struct SiteExtra {
 #ifndef LBF_FWD_MINB_Q27_16
 #define LBF_FWD_MINB_Q27_16 2
 #endif
-constexpr int fwd_rows(int Q, int bytes) {
+// D3Q27 without walls: its ring needs one c_z = -1 slot less, and shorter tiles then fit 3 CTAs
+// per SM (FP32: 6 rows, 72.6 KB; 16-bit: 7 rows, 70.3 KB; measured +4% over 8-row tiles at 2 CTAs)
+#ifndef LBF_FWD_ROWS_Q27_NM
+#define LBF_FWD_ROWS_Q27_NM 6
+#endif
+#ifndef LBF_FWD_MINB_Q27_NM
+#define LBF_FWD_MINB_Q27_NM 3
+#endif
+#ifndef LBF_FWD_ROWS_Q27_16_NM
+#define LBF_FWD_ROWS_Q27_16_NM 7
+#endif
+#ifndef LBF_FWD_MINB_Q27_16_NM
+#define LBF_FWD_MINB_Q27_16_NM 3
+#endif
+constexpr int fwd_rows(int Q, int bytes, bool mask = true) {
   return bytes == 8 ? LBF_FWD_ROWS_F64
-                    : (bytes == 4 ? (Q == 19 ? LBF_FWD_ROWS_Q19 : LBF_FWD_ROWS_Q27)
-                                  : (Q == 19 ? LBF_FWD_ROWS_Q19_16 : LBF_FWD_ROWS_Q27_16));
+                    : (bytes == 4 ? (Q == 19 ? LBF_FWD_ROWS_Q19 : (mask ? LBF_FWD_ROWS_Q27 : LBF_FWD_ROWS_Q27_NM))
+                                  : (Q == 19 ? LBF_FWD_ROWS_Q19_16 : (mask ? LBF_FWD_ROWS_Q27_16 : LBF_FWD_ROWS_Q27_16_NM)));
 }
-constexpr int fwd_minb(int Q, int bytes) {
+constexpr int fwd_minb(int Q, int bytes, bool mask = true) {
   return bytes == 8 ? 1
-                    : (bytes == 4 ? (Q == 19 ? LBF_FWD_MINB_Q19 : LBF_FWD_MINB_Q27)
-                                  : (Q == 19 ? LBF_FWD_MINB_Q19_16 : LBF_FWD_MINB_Q27_16));
+                    : (bytes == 4 ? (Q == 19 ? LBF_FWD_MINB_Q19 : (mask ? LBF_FWD_MINB_Q27 : LBF_FWD_MINB_Q27_NM))
+                                  : (Q == 19 ? LBF_FWD_MINB_Q19_16 : (mask ? LBF_FWD_MINB_Q27_16 : LBF_FWD_MINB_Q27_16_NM)));
 }
 
 constexpr uint32_t kWaitPolls = 1u << 20;  // bound of every mbarrier wait
@@ -359,11 +376,11 @@ constexpr uint32_t kWaitPolls = 1u << 20;  // bound of every mbarrier wait
 #endif
 
 template <class L, class S, int BY, bool MASK, bool TWO, bool FF, bool TMA, bool RN>
-__global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeof(S))))
+__global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeof(S)), MASK))
     k_stream_collide(const FwdParams a, const __grid_constant__ CUtensorMap tmap) {
   using T = typename ComputeOf<S>::type;
   using D = Dirs<L>;
-  using R = GroupRing<L, BY + 2>;
+  using R = GroupRing<L, BY + 2, MASK>;
   constexpr int Q = L::Q;
   constexpr int ROWS = BY + 2;
   constexpr int SITES = ROWS * 32;
@@ -544,7 +561,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     const T Fs0 = SITEF ? e.F[0] : Fu0, Fs1 = SITEF ? e.F[1] : Fu1, Fs2 = SITEF ? e.F[2] : Fu2;
     const PostColl<T> P =
         post_collision<T>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9], Fs0, Fs1, Fs2, inv2rho, omm);
-    T* w0 = ring + R::base(0) + par * G0 + me;
+    T* w0 = ring + R::base(0) + (R::NS0 == 2 ? par : 0) * G0 + me;
     T* w1 = ring + R::base(1) + par * G1 + me;
     T* w2 = ring + R::base(2) + g2 + me;
     auto put = [&](auto qc, T v) {
@@ -655,12 +672,12 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     }
     if (out_row) {
       // pull bases: group c_z = -1 from plane z+1, c_z = 0 from plane z, c_z = +1 from plane z-1
-      const T* P0 = ring + R::base(0) + PAR * G0 + me;
+      const T* P0 = ring + R::base(0) + (R::NS0 == 2 ? PAR : 0) * G0 + me;
       const T* P1 = ring + R::base(1) + (PAR ^ 1) * G1 + me;
       const T* P2 = ring + R::base(2) + g2m + me;
       auto gather = [&](auto walls_c) {
         constexpr bool W = decltype(walls_c)::value;
-        const T* O0 = ring + R::base(0) + (PAR ^ 1) * G0 + me;  // own site, plane z
+        const T* O0 = ring + R::base(0) + (R::NS0 == 2 ? (PAR ^ 1) : 0) * G0 + me;  // own site, plane z (walls only)
         const T* O2 = ring + R::base(2) + g20 + me;
         const uint8_t* MM = msk + g2m / GS2 + me;
         const uint8_t* M0 = msk + g20 / GS2 + me;
