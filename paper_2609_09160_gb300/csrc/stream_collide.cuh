@@ -203,6 +203,80 @@ __device__ __forceinline__ void accumulate_pair(Accum<T>& A, T gq, T go, T w) {
   A.ryz = sfma<cy * cz>(A.ryz, w, s);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Packed FP32 accumulation (FFMA2/FADD2: two FP32 lanes per instruction on sm_100 and later).
+// The non-axial direction pairs are taken two at a time ("couples"), preferring two pairs with the
+// same |c_x|, |c_y|, |c_z| so that both lanes feed the same moments; each moment keeps two partial
+// sums (lane 0: first pair, lane 1: second pair) that are added once at the end.
+template <class L>
+struct Couples {
+  __host__ __device__ static constexpr bool rep(int q) {  // one direction of each non-axial pair
+    return q < L::opp(q) && !(L::cx(q) == 0 && L::cy(q) == 0);
+  }
+  __host__ __device__ static constexpr int support(int q) {
+    return 4 * (L::cx(q) != 0) + 2 * (L::cy(q) != 0) + (L::cz(q) != 0);
+  }
+  __host__ __device__ static constexpr int count() {
+    int n = 0;
+    for (int q = 0; q < L::Q; ++q)
+      if (rep(q)) ++n;
+    return n / 2;
+  }
+  // first and second pair of couple k: greedy, same support first, then any
+  __host__ __device__ static constexpr int member(int k, int which) {
+    bool used[27] = {};
+    for (int c = 0; c <= k; ++c) {
+      int qa = -1, qb = -1;
+      for (int q = 0; q < L::Q && qa < 0; ++q)
+        if (rep(q) && !used[q]) qa = q;
+      if (qa < 0) return -1;
+      used[qa] = true;
+      for (int q = 0; q < L::Q && qb < 0; ++q)
+        if (rep(q) && !used[q] && support(q) == support(qa)) qb = q;
+      for (int q = 0; q < L::Q && qb < 0; ++q)
+        if (rep(q) && !used[q]) qb = q;
+      if (qb < 0) return -1;
+      used[qb] = true;
+      if (c == k) return which == 0 ? qa : qb;
+    }
+    return -1;
+  }
+};
+
+struct Accum2 {
+  float2 a0, jx, jy, jz, rxx, ryy, rzz, rxy, rxz, ryz;
+};
+
+// acc + (CA wa, CB wb) v, elementwise, for compile-time CA, CB in {-1, 0, 1}
+template <int CA, int CB>
+__device__ __forceinline__ void pfma(float2& acc, float wa, float wb, float2 v) {
+  if constexpr (CA != 0 || CB != 0) acc = __ffma2_rn(make_float2(float(CA) * wa, float(CB) * wb), v, acc);
+}
+
+// adds the two pairs of a couple: lane 0 (g.x, o.x) along qa and its opposite, lane 1 along qb
+template <class L, int qa, int qb>
+__device__ __forceinline__ void accumulate_couple(Accum2& A, float2 g, float2 o) {
+  constexpr float wa = float(L::w(qa)), wb = float(L::w(qb));
+  constexpr int ax = L::cx(qa), ay = L::cy(qa), az = L::cz(qa);
+  constexpr int bx = L::cx(qb), by = L::cy(qb), bz = L::cz(qb);
+  const float2 s = __fadd2_rn(g, o);
+  const float2 d = __ffma2_rn(o, make_float2(-1.0f, -1.0f), g);
+  A.a0 = __ffma2_rn(make_float2(wa, wb), s, A.a0);
+  pfma<ax, bx>(A.jx, wa, wb, d);
+  pfma<ay, by>(A.jy, wa, wb, d);
+  pfma<az, bz>(A.jz, wa, wb, d);
+  pfma<ax * ax, bx * bx>(A.rxx, wa, wb, s);
+  pfma<ay * ay, by * by>(A.ryy, wa, wb, s);
+  pfma<az * az, bz * bz>(A.rzz, wa, wb, s);
+  pfma<ax * ay, bx * by>(A.rxy, wa, wb, s);
+  pfma<ax * az, bx * bz>(A.rxz, wa, wb, s);
+  pfma<ay * az, by * bz>(A.ryz, wa, wb, s);
+}
+
+#ifndef LBF_PACKED_ACC
+#define LBF_PACKED_ACC 1
+#endif
+
 template <int BY>
 struct FwdTile {
   static constexpr int ROWS = BY + 2;
@@ -491,7 +565,10 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     else e.solid = false;
   };
 
-  // the 10 stored values of this thread's site in plane p (raw stage `st` when staged by TMA)
+  // the 10 stored values of this thread's site in plane p (raw stage `st` when staged by TMA).
+  // With scaled 16-bit storage the six N fields are returned in storage units: N enters the
+  // post-collision moments only through (1 - omega) N, so its power-of-two decode factor is applied
+  // to (1 - omega) instead (exact, one multiply instead of six)
   auto read_raw = [&](int p, int st, T (&m)[10]) {
     if (TMA && inbox) {
       const S* b = raw_me + st * STAGE_STRIDE;
@@ -499,9 +576,10 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
                              (b - rawst) + 9 * ROWS * BX < kRawStages * STAGE_STRIDE);
 #pragma unroll
       for (int k = 0; k < 10; ++k) {
-        const float dec = k == 0 ? a.sc.dec[0] : (k < 4 ? a.sc.dec[1] : a.sc.dec[2]);
+        const float dec = k == 0 ? a.sc.dec[0] : a.sc.dec[1];
         if constexpr (Codec<S>::scaled)
-          m[k] = static_cast<T>(static_cast<float>(b[k * ROWS * BX]) * dec);
+          m[k] = k < 4 ? static_cast<T>(static_cast<float>(b[k * ROWS * BX]) * dec)
+                       : static_cast<T>(static_cast<float>(b[k * ROWS * BX]));
         else
           m[k] = static_cast<T>(b[k * ROWS * BX]);
       }
@@ -509,7 +587,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
       const S* __restrict__ bz = src + (long long)wrap(p, a.nz) * plane;
 #pragma unroll
       for (int k = 0; k < 10; ++k) {
-        const float dec = k == 0 ? a.sc.dec[0] : (k < 4 ? a.sc.dec[1] : a.sc.dec[2]);
+        const float dec = k == 0 ? a.sc.dec[0] : (k < 4 ? a.sc.dec[1] : 1.0f);
         m[k] = ld_field<S, T>(bz + k * N, col, dec);
       }
     } else {
@@ -534,9 +612,12 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   int g2m = 0, g20 = G2, g2p = 2 * G2;
 
   // -- staging: post-collision populations of plane p into the ring ----------------------------
-  // par: (p - pbase) & 1 (compile time); g2: the three-slot offset of plane p
-  auto stage = [&](auto par_c, int p, int g2, const SiteExtra<T, TWO>& e) -> bool {
+  // par: (p - pbase) & 1 (compile time); g2: the three-slot offset of plane p. halo: 0 for the
+  // output rows (every direction); +1 / -1 for the y-halo row below / above the tile, which is
+  // pulled only along the directions with c_y = +1 / -1 and stages only those
+  auto stage = [&](auto par_c, auto halo_c, int p, int g2, const SiteExtra<T, TWO>& e) -> bool {
     constexpr int par = decltype(par_c)::value;
+    constexpr int H = decltype(halo_c)::value;
     T m[10];
     // raw stage of plane p: (p - pbase) mod kRawStages, the plane parity when there are two
     read_raw(p, kRawStages == 2 ? par : (p - pbase) % kRawStages, m);
@@ -559,6 +640,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
       Fnext[2] = e.F[2];
     }
     const T Fs0 = SITEF ? e.F[0] : Fu0, Fs1 = SITEF ? e.F[1] : Fu1, Fs2 = SITEF ? e.F[2] : Fu2;
+    if constexpr (Codec<S>::scaled) omm *= a.sc.dec[2];  // N is in storage units (read_raw)
     const PostColl<T> P =
         post_collision<T>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9], Fs0, Fs1, Fs2, inv2rho, omm);
     T* w0 = ring + R::base(0) + (R::NS0 == 2 ? par : 0) * G0 + me;
@@ -579,18 +661,29 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     };
     static_for<Q>([&](auto qc) {
       constexpr int q = decltype(qc)::value;
+      constexpr bool need_q = H == 0 || L::cy(q) == H, need_o = H == 0 || L::cy(L::opp(q)) == H;
       if constexpr (q == QREST) {
-        rest_new = P.q0;
-      } else if constexpr (q < L::opp(q)) {
+        if constexpr (H == 0) rest_new = P.q0;
+      } else if constexpr (q < L::opp(q) && (need_q || need_o)) {
         T fq, fo;
         pop_pair<L, q, T>(P, fq, fo);
-        put(qc, fq);
-        put(std::integral_constant<int, L::opp(q)>{}, fo);
+        if constexpr (need_q) put(qc, fq);
+        if constexpr (need_o) put(std::integral_constant<int, L::opp(q)>{}, fo);
       }
     });
     if constexpr (MASK) msk[g2 / GS2 + me] = e.solid ? 1 : 0;
     sol_new = e.solid;
     return e.solid;
+  };
+
+  // the reduced halo staging pays on D3Q27 (9 of 26 directions per halo row); on D3Q19 (5 of 18)
+  // the extra code measured slower than staging every direction
+  auto stage_row = [&](auto par_c, int p, int g2, const SiteExtra<T, TWO>& e) -> bool {
+    if constexpr (L::Q == 27) {
+      if (row == 0) return stage(par_c, std::integral_constant<int, 1>{}, p, g2, e);
+      if (row == ROWS - 1) return stage(par_c, std::integral_constant<int, -1>{}, p, g2, e);
+    }
+    return stage(par_c, std::integral_constant<int, 0>{}, p, g2, e);
   };
 
   T red[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -623,7 +716,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   if constexpr (TMA) {
     wait_plane(z0 - 1);
   }
-  bool any_m = stage(std::integral_constant<int, 0>{}, z0 - 1, g2m, ex);
+  bool any_m = stage_row(std::integral_constant<int, 0>{}, z0 - 1, g2m, ex);
   up_m1 = up_new;
   sol_m1 = sol_new;
   load_extra(z0, ex);
@@ -635,7 +728,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     if (me == 0) issue(z0 - 1 + kRawStages);
     wait_plane(z0);
   }
-  bool any_0 = stage(std::integral_constant<int, 1>{}, z0, g20, ex);
+  bool any_0 = stage_row(std::integral_constant<int, 1>{}, z0, g20, ex);
   if constexpr (TMA) {
     if (!out_row) wait_plane(z0 + 1);  // staged by the first iteration (z0 + 1 <= z1)
   }
@@ -661,7 +754,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     constexpr int PAR = decltype(par_c)::value;
     // plane z+1 has landed: the y-halo warps waited for it before the barrier that ended the
     // previous iteration (or the prologue), and that barrier orders the observation for everyone
-    bool any_p = stage(std::integral_constant<int, PAR>{}, z + 1, g2p, ex);
+    bool any_p = stage_row(std::integral_constant<int, PAR>{}, z + 1, g2p, ex);
     load_extra(z + 2, ex);  // in flight during the outputs of plane z (z + 2 <= nz + 1 wraps)
     if constexpr (MASK)
       any_p = __syncthreads_or(any_p);
@@ -702,14 +795,39 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
           }
           return v;
         };
-        static_for<Q>([&](auto qc) {
-          constexpr int q = decltype(qc)::value;
-          if constexpr (q != QREST && q < L::opp(q) && q != QUP && q != QDN) {
-            const T fq = pulled(qc);
-            const T fo = pulled(std::integral_constant<int, L::opp(q)>{});
-            accumulate_pair<L::cx(q), L::cy(q), L::cz(q), T>(A, fq, fo, T(L::w(q)));
-          }
-        });
+        if constexpr (std::is_same<T, float>::value && L::Q == 27 && LBF_PACKED_ACC) {
+          using C = Couples<L>;
+          const float2 z2 = make_float2(0.0f, 0.0f);
+          Accum2 A2 = {z2, z2, z2, z2, z2, z2, z2, z2, z2, z2};
+          static_for<C::count()>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int qa = C::member(k, 0), qb = C::member(k, 1);
+            static_assert(qa >= 0 && qb >= 0, "direction couples");
+            const float2 g = make_float2(pulled(std::integral_constant<int, qa>{}), pulled(std::integral_constant<int, qb>{}));
+            const float2 o = make_float2(pulled(std::integral_constant<int, L::opp(qa)>{}),
+                                         pulled(std::integral_constant<int, L::opp(qb)>{}));
+            accumulate_couple<L, qa, qb>(A2, g, o);
+          });
+          A.a0 += A2.a0.x + A2.a0.y;
+          A.jx = A2.jx.x + A2.jx.y;
+          A.jy = A2.jy.x + A2.jy.y;
+          A.jz = A2.jz.x + A2.jz.y;
+          A.rxx = A2.rxx.x + A2.rxx.y;
+          A.ryy = A2.ryy.x + A2.ryy.y;
+          A.rzz = A2.rzz.x + A2.rzz.y;
+          A.rxy = A2.rxy.x + A2.rxy.y;
+          A.rxz = A2.rxz.x + A2.rxz.y;
+          A.ryz = A2.ryz.x + A2.ryz.y;
+        } else {
+          static_for<Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            if constexpr (q != QREST && q < L::opp(q) && q != QUP && q != QDN) {
+              const T fq = pulled(qc);
+              const T fo = pulled(std::integral_constant<int, L::opp(q)>{});
+              accumulate_pair<L::cx(q), L::cy(q), L::cz(q), T>(A, fq, fo, T(L::w(q)));
+            }
+          });
+        }
         // axial pair: (0,0,+1) comes from the plane below, (0,0,-1) from the plane above
         T fup = up_m1, fdn = dn_new;
         if constexpr (W) {
