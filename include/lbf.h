@@ -18,11 +18,12 @@
  *  - Internal state ("state buffer"): the same 10 fields in the storage dtype, with the tensor
  *    stored as N = A - u u and, for 16-bit storage, every group multiplied by a power of two.
  *    Callers treat it as opaque bytes of size lbf_state_bytes().
- *  - 16-bit storage: by default a time step rounds the values it stores stochastically
- *    (unbiased), with random bits from a counter-based generator keyed by the site and the
- *    context's count of steps taken, so results are bitwise reproducible for the same sequence of
- *    calls; lbf_params.rounding selects round-to-nearest instead. Loading a state
- *    (lbf_set_moments) always rounds to nearest.
+ *  - 16-bit storage: by default a time step rounds the p* and u values it stores
+ *    stochastically (unbiased), with random bits from a counter-based generator keyed by the site
+ *    and the context's count of steps taken, so results are bitwise reproducible for the same
+ *    sequence of calls; lbf_params.rounding selects round-to-nearest instead. The N fields, which
+ *    a step recomputes rather than accumulates, and every value loaded by lbf_set_moments round
+ *    to nearest.
  *  - Every call is ordered on the context's CUDA stream (lbf_params.stream) and returns without
  *    waiting for the GPU, except lbf_reduce and lbf_synchronize, which wait for the stream.
  *  - The library allocates no device memory: the caller provides one workspace of

@@ -83,10 +83,11 @@ __device__ __forceinline__ void static_for(F&& f) {
 template <class S>
 struct Codec;
 
-// store: round to nearest (loading a state). store_sr: unbiased stochastic rounding with the
-// random word r, used by the time step. Round-to-nearest of a 16-bit state discards every update
-// smaller than half a unit in the last place: on large lattices, where the flow changes by less
-// than 2^-12 of its value per step, the state then freezes and its error grows with time.
+// store: round to nearest (loading a state; the N fields of a step). store_sr: unbiased
+// stochastic rounding with the random word r, used by the time step for p* and u. Round-to-nearest
+// of a 16-bit state discards every update smaller than half a unit in the last place: on large
+// lattices, where the flow changes by less than 2^-12 of its value per step, the state then
+// freezes and its error grows with time.
 // Adding uniform random bits below the kept significand and truncating rounds up with
 // probability equal to the discarded fraction, so the expected stored value is exact.
 template <>

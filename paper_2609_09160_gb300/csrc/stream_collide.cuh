@@ -864,18 +864,22 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
         LBF_CHECK(a.flags, z >= 0 && z < a.nz && col >= 0 && col < plane && zc + 9 * N < 10 * N);
         // random sequence of this site and step (16-bit storage only)
         {
-          // 16-bit storage rounds stochastically unless RN (round to nearest); FP32/FP64 stores are plain
+          // 16-bit storage rounds p* and u stochastically unless RN (round to nearest); the six N
+          // fields always round to nearest: N is recomputed from the populations every step rather
+          // than accumulated, so its small changes are never lost (stochastic rounding of N gave the
+          // same error at 64^3 and 512^3 and costs two instructions per field). FP32/FP64 stores
+          // are plain.
           uint32_t rs = Codec<S>::scaled && !RN ? fmix32(uint32_t(zc) ^ a.salt) : 0u;
           st_field<S, RN>(dst, zc, A.a0, a.sc.enc[0], rs);
           st_field<S, RN>(dst + N, zc, ux, a.sc.enc[1], rs);
           st_field<S, RN>(dst + 2 * N, zc, uy, a.sc.enc[1], rs);
           st_field<S, RN>(dst + 3 * N, zc, uz, a.sc.enc[1], rs);
-          st_field<S, RN>(dst + 4 * N, zc, nxx, a.sc.enc[2], rs);
-          st_field<S, RN>(dst + 5 * N, zc, nyy, a.sc.enc[2], rs);
-          st_field<S, RN>(dst + 6 * N, zc, nzz, a.sc.enc[2], rs);
-          st_field<S, RN>(dst + 7 * N, zc, nxy, a.sc.enc[2], rs);
-          st_field<S, RN>(dst + 8 * N, zc, nxz, a.sc.enc[2], rs);
-          st_field<S, RN>(dst + 9 * N, zc, nyz, a.sc.enc[2], rs);
+          st_field<S, true>(dst + 4 * N, zc, nxx, a.sc.enc[2], rs);
+          st_field<S, true>(dst + 5 * N, zc, nyy, a.sc.enc[2], rs);
+          st_field<S, true>(dst + 6 * N, zc, nzz, a.sc.enc[2], rs);
+          st_field<S, true>(dst + 7 * N, zc, nxy, a.sc.enc[2], rs);
+          st_field<S, true>(dst + 8 * N, zc, nxz, a.sc.enc[2], rs);
+          st_field<S, true>(dst + 9 * N, zc, nyz, a.sc.enc[2], rs);
         }
         if (!(uu <= T(a.umax2))) atomicOr(a.flags, 1u);
         red[0] += A.a0;
