@@ -6,7 +6,8 @@ imports it and shares no code with it; the two meet only through the seeded inpu
 of the `synth` package, which hold none of the method's arithmetic.
 
 Modules
-  lattice      D3Q19 / D3Q27 velocity sets and the second-order Hermite basis (textbook values)
+  lattice      D3Q19 / D3Q27 velocity sets, the second-order Hermite basis (textbook values) and
+               the complete D3Q27 Hermite basis of D3Q27h
   lbm          population-form step: Hermite projection, Eq. (corr), regularized collision with
                Guo forcing, Eq. (pullLB), pull streaming with halfway bounce-back
   moment_form  literal site-by-site transcription of Eq. (pullLLB) + Eq. (corr), tiny lattices
@@ -18,4 +19,4 @@ Parity status: every function is pinned by tests/test_oracle_*.py against closed
 invariants, textbook identities, brute force or finite differences; none is "parity unpinned".
 """
 from . import adjoint, diagnostics, lattice, lbm, moment_form, phase  # noqa: F401
-from .lattice import CS2, D3Q19, D3Q27  # noqa: F401
+from .lattice import CS2, D3Q19, D3Q27, D3Q27H  # noqa: F401

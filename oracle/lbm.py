@@ -120,9 +120,67 @@ def moments_from_populations(lat, f, F, rho):
     return pack(p, u, A)
 
 
+def _prod(fields, like):
+    out = torch.ones_like(like)
+    for v in fields:
+        out = out * v
+    return out
+
+
+def full_coefficients(lat, p, u, a2neq, F, rho, omega):
+    """Post-collision Hermite coefficients of D3Q27h for every multi-index m of the complete
+    D3Q27 basis (Sec. 2, higher-order formulation with the recursive closure of Shan et al. and
+    Malaspinas), in the velocity-pressure form of the paper. With alpha = axes_of(m), n = |alpha|:
+      equilibrium      a_eq(m)  = p* (n = 0), u_alpha1 ... u_alphan (n >= 1)
+      non-equilibrium  a_neq(m) = 0 (n < 2), N_alpha1alpha2 (n = 2), and for n >= 3 the closure
+                       sum over index pairs {i, j} of N_alphai alphaj prod_{k not i, j} u_alphak
+      Guo source       S(m)     = sum over positions i of F_alphai prod_{k != i} u_alphak / rho
+    and P(m) = a_eq + (1 - omega) a_neq + S/2 (the bracket of Eq. pullLB). Truncated at n <= 2
+    this is exactly the second-order scheme of `collide`. Returns a list in MULTI order."""
+    from .lattice import MULTI, axes_of
+    coefs = []
+    for m in MULTI:
+        al = axes_of(m)
+        n = len(al)
+        if n == 0:
+            coefs.append(p)
+            continue
+        eq = _prod([u[a] for a in al], p)
+        if n < 2:
+            neq = torch.zeros_like(p)
+        else:
+            neq = torch.zeros_like(p)
+            for i in range(n):
+                for j in range(i + 1, n):
+                    rest = [u[al[k]] for k in range(n) if k != i and k != j]
+                    neq = neq + a2neq[al[i], al[j]] * _prod(rest, p)
+        src = torch.zeros_like(p)
+        for i in range(n):
+            rest = [u[al[k]] for k in range(n) if k != i]
+            src = src + F[al[i]] * _prod(rest, p)
+        src = src / rho
+        coefs.append(eq + (1.0 - omega) * neq + 0.5 * src)
+    return coefs
+
+
+def full_reconstruct(lat, coefs):
+    """f_i = w_i sum_m H_m(c_i) P(m) / norm(m) over the complete D3Q27 basis."""
+    P = torch.stack(coefs, dim=0)
+    g = torch.einsum("mq,m...->q...", lat.HM / lat.HM_norm.unsqueeze(1), P)
+    return _wq(lat, coefs[0]) * g
+
+
 def collide(lat, f, F, rho, omega):
     """Right-hand side of Eq. (pullLB) at every site, before streaming:
-    f_post = f_eq + (1 - omega) f_neq + S/2 with the regularized f_neq."""
+    f_post = f_eq + (1 - omega) f_neq + S/2 with the regularized f_neq (second order), or the
+    same bracket over the complete Hermite basis for D3Q27h (lat.high)."""
+    if lat.high:
+        p, u, A = macroscopic(lat, f, F, rho)
+        uu = torch.einsum("a...,b...->ab...", u, u)
+        S = guo_source(lat, u, F, rho)
+        fneq_raw = f - hermite_reconstruct(lat, p, u, uu) + 0.5 * S
+        _, _, a2neq = hermite_project(lat, fneq_raw)  # = A - u u
+        return full_reconstruct(lat, full_coefficients(lat, p, u, a2neq, F, rho, omega))
     p, u, A = macroscopic(lat, f, F, rho)
     uu = torch.einsum("a...,b...->ab...", u, u)
     feq = hermite_reconstruct(lat, p, u, uu)  # a_eq = (p*, u, u u)
