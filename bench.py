@@ -142,6 +142,8 @@ def gpu_identifier(torch, dev):
         return str(dev)
 
 
+LATTICE_NAME = {19: "D3Q19", 27: "D3Q27", 127: "D3Q27h"}
+
 WORKLOADS = {
     # key: (lattice, storage, builder) -- the headline is "channel256"
     "channel256": (19, "f32", "channel"),
@@ -150,6 +152,8 @@ WORKLOADS = {
     "tg512_d3q27_bf16": (27, "bf16", "tg512"),
     "tg512_d3q19_f32": (19, "f32", "tg512"),
     "tg512_d3q19_f16": (19, "f16", "tg512"),
+    "tg512_d3q27h_f32": (127, "f32", "tg512"),
+    "tg512_d3q27h_f16": (127, "f16", "tg512"),
     "droplet128": (19, "f32", "droplet"),
     "adjoint128": (19, "f32", "adjoint"),
 }
@@ -313,11 +317,12 @@ def extras(torch, device, quick):
 
     n = 512
     M0 = synth.taylor_green_perturbed(n, 0.04, 0.55, 0.01, seed=3, dtype=torch.float32, device=device)
-    for lattice in (27, 19):
+    for lattice in (27, 19, 127):  # 127: D3Q27h (complete Hermite basis)
         for storage in ("f32", "f16", "bf16"):
             s = Solver((n, n, n), lattice=lattice, tau=0.55, storage=storage, device=device)
             s.set_moments(M0)
-            out[f"tg512_d3q{lattice}_{storage}"] = rate(s, 30 if quick else 100, 5, algorithmic_bytes(storage))
+            out[f"tg512_{LATTICE_NAME[lattice].lower()}_{storage}"] = rate(s, 30 if quick else 100, 5,
+                                                                           algorithmic_bytes(storage))
             del s
             torch.cuda.empty_cache()
     del M0
@@ -429,14 +434,14 @@ def run_ours(args):
     traffic = ncu_traffic(args.workload)
     desc = {"channel": WORKLOAD,
             "droplet": "two-component D3Q19 FP32 128^3 static droplet R=20, W=4, sigma=0.03, D=0.1, tau=1",
-            "tg512": (f"D3Q{lattice} {storage.upper()} storage, 512^3 periodic Taylor-Green U0=0.04 + random-phase "
+            "tg512": (f"{LATTICE_NAME[lattice]} {storage.upper()} storage, 512^3 periodic Taylor-Green U0=0.04 + random-phase "
                       "perturbation RMS 0.01 (seed 3), tau=0.55")}[kind]
     shape_xyz = {"channel": [256, 256, 256], "droplet": [128, 128, 128], "tg512": [512, 512, 512]}[kind]
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if storage == "f64" else "f32", "data": "synthetic",
-        "config": {"workload": desc, "lattice": f"D3Q{lattice}", "shape_xyz": shape_xyz, "storage": storage,
+        "config": {"workload": desc, "lattice": LATTICE_NAME[lattice], "shape_xyz": shape_xyz, "storage": storage,
                    "l2": "inputs larger than L2 (two moment buffers of >= 671 MB), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

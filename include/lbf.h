@@ -7,7 +7,10 @@
  * Eq. (pullLLB): every site rebuilds the regularized post-collision populations of its Q
  * neighbours (Eqs. reqtfeq, hermite_teq) including the Guo source (Eq. guoforce), streams them
  * in and takes their moments, followed by the half-force correction of Eq. (corr). D3Q19 and
- * D3Q27 with second-order truncation are supported. The conservative Allen-Cahn phase field of
+ * D3Q27 with second-order truncation are supported, and D3Q27h: the D3Q27 velocities with the
+ * complete Hermite basis, whose third- to sixth-order coefficients are rebuilt from the stored
+ * moments by the recursive closure (Sec. 2; the state is the same 10 fields). The conservative
+ * Allen-Cahn phase field of
  * Eq. (ACeq) with the capillary force provides the two-component coupling at equal densities.
  *
  * Conventions shared by every call
@@ -45,7 +48,11 @@ extern "C" {
 
 typedef struct lbf_ctx lbf_ctx; /* opaque, host-side; owns no device memory */
 
-enum { LBF_D3Q19 = 19, LBF_D3Q27 = 27 };
+/* lattices: D3Q19 and D3Q27 truncated at second order; D3Q27H = D3Q27 velocities with the complete
+   Hermite basis (post-collision coefficient of every supported multi-index m: u^m + (1 - omega)
+   times the closure of N + half the Guo source, Sec. 2). D3Q27H has no adjoint and no population
+   representation (LBF_ENOTSUP). */
+enum { LBF_D3Q19 = 19, LBF_D3Q27 = 27, LBF_D3Q27H = 127 };
 
 /* storage / transfer dtypes; F64 storage computes in FP64, every other storage in FP32 */
 enum { LBF_F64 = 0, LBF_F32 = 1, LBF_F16 = 2, LBF_BF16 = 3 };
@@ -67,7 +74,7 @@ typedef enum {
 } lbf_status;
 
 typedef struct {
-  int lattice;          /* LBF_D3Q19 or LBF_D3Q27 */
+  int lattice;          /* LBF_D3Q19, LBF_D3Q27 or LBF_D3Q27H */
   int nx, ny, nz;       /* >= 1 each */
   int storage;          /* LBF_F64, LBF_F32, LBF_F16 or LBF_BF16 */
   double tau;           /* single-component relaxation time, > 0.5; nu = (tau - 1/2)/3

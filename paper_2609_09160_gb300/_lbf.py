@@ -8,7 +8,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 # LBF_LIBRARY selects another build of the same library (e.g. the index-checked liblbf_debug.so)
 LIB_PATH = os.environ.get("LBF_LIBRARY") or os.path.join(_PKG, "liblbf.so")
 
-LBF_D3Q19, LBF_D3Q27 = 19, 27
+LBF_D3Q19, LBF_D3Q27, LBF_D3Q27H = 19, 27, 127
 LBF_F64, LBF_F32, LBF_F16, LBF_BF16 = 0, 1, 2, 3
 LBF_OK, LBF_EINVAL, LBF_ENOMEM, LBF_ECUDA, LBF_EUNSTABLE, LBF_EINTERNAL, LBF_ENOTSUP = range(7)
 LBF_ROUND_STOCHASTIC, LBF_ROUND_NEAREST = 0, 1

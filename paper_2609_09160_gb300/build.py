@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbf.so")
 SOURCES = ["api.cu", "static_step.cu", "kernels.cu"]
 # kernels.cu is compiled once per (lattice, storage) pair; each object holds that pair's kernels
-KERNEL_UNITS = [(q, s) for q in (19, 27) for s in range(4)]
+KERNEL_UNITS = [(q, s) for q in (19, 27, 127) for s in range(4)]  # 127: D3Q27h
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-O2", "-I", os.path.join(ROOT, "include")]

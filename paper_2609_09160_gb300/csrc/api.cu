@@ -65,7 +65,10 @@ struct Layout {
 
 lbf_status check_params(const lbf_params* p) {
   if (p == nullptr) return fail(LBF_EINVAL, "params is NULL");
-  if (p->lattice != LBF_D3Q19 && p->lattice != LBF_D3Q27) return fail(LBF_EINVAL, "lattice must be 19 or 27");
+  if (p->lattice != LBF_D3Q19 && p->lattice != LBF_D3Q27 && p->lattice != LBF_D3Q27H)
+    return fail(LBF_EINVAL, "lattice must be LBF_D3Q19, LBF_D3Q27 or LBF_D3Q27H");
+  if (p->lattice == LBF_D3Q27H && p->populations)
+    return fail(LBF_ENOTSUP, "the population representation collides at second order (D3Q19, D3Q27)");
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LBF_EINVAL, "nx, ny, nz must be >= 1");
   const double n = double(p->nx) * double(p->ny) * double(p->nz);
   if (n > 4.0e10) return fail(LBF_EINVAL, "lattice too large");
@@ -98,7 +101,9 @@ lbf_status check_params(const lbf_params* p) {
 
 int grid_x(int nx) { return (nx + FwdTile<8>::XOUT - 1) / FwdTile<8>::XOUT; }
 int grid_y(int ny, int by) { return (ny + by - 1) / by; }
-int fwd_by(int Q, int storage, bool mask) { return fwd_rows(Q, int(storage_bytes(storage)), mask); }
+int fwd_by(int lattice, int storage, bool mask, bool two) {
+  return fwd_rows(lattice == LBF_D3Q19 ? 19 : 27, int(storage_bytes(storage)), mask, two);
+}
 int min_zchunk(int nz) { return std::min(8, nz); }
 
 bool make_layout(const lbf_params* p, Layout* L) {
@@ -128,7 +133,7 @@ bool make_layout(const lbf_params* p, Layout* L) {
     L->phi[0] = L->phi[1] = L->F[0] = L->F[1] = L->G = 0;
   }
   const long long gz = (p->nz + min_zchunk(p->nz) - 1) / min_zchunk(p->nz);
-  L->npartials = std::max<long long>((long long)grid_x(p->nx) * grid_y(p->ny, fwd_by(p->lattice, p->storage, p->mask != nullptr)) * gz, 1024);
+  L->npartials = std::max<long long>((long long)grid_x(p->nx) * grid_y(p->ny, fwd_by(p->lattice, p->storage, p->mask != nullptr, p->two_component != 0)) * gz, 1024);
   L->partials = take(size_t(L->npartials) * 8 * sizeof(double));
   L->scal = take(64 * sizeof(double));
   L->staging_bytes = std::min<size_t>(kStagingMax, size_t(11) * 8 * size_t(N));
@@ -892,6 +897,7 @@ lbf_status lbf_adjoint_step(lbf_ctx* c, const void* state_t, const void* state_t
     return fail(LBF_EINVAL, "bad argument");
   if (c->two) return fail(LBF_ENOTSUP, "the adjoint is single-component only");
   if (c->pops) return fail(LBF_ENOTSUP, "the adjoint works on the moment representation");
+  if (c->Q == LBF_D3Q27H) return fail(LBF_ENOTSUP, "the adjoint is that of the second-order step (D3Q19, D3Q27)");
   if (c->adj.fn == nullptr) return fail(LBF_ENOTSUP, "the adjoint needs LBF_F32 or LBF_F64 storage");
   AdjParams a;
   std::memset(&a, 0, sizeof(a));

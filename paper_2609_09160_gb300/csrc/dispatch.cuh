@@ -25,7 +25,7 @@ struct KernelInfo {
 
 template <class L, class S, bool MASK, bool TWO, bool FF, bool TMA, bool RN>
 KernelInfo fwd_info() {
-  constexpr int BY = fwd_rows(L::Q, int(sizeof(S)), MASK);
+  constexpr int BY = fwd_rows(L::Q, int(sizeof(S)), MASK, TWO);
   KernelInfo k;
   k.fn = reinterpret_cast<const void*>(&k_stream_collide<L, S, BY, MASK, TWO, FF, TMA, RN>);
   k.smem = fwd_smem_bytes<L, S, BY, MASK, TMA>();
@@ -109,11 +109,25 @@ LBF_DECLARE_TU(27, 0)
 LBF_DECLARE_TU(27, 1)
 LBF_DECLARE_TU(27, 2)
 LBF_DECLARE_TU(27, 3)
+LBF_DECLARE_TU(127, 0)
+LBF_DECLARE_TU(127, 1)
+LBF_DECLARE_TU(127, 2)
+LBF_DECLARE_TU(127, 3)
 #undef LBF_DECLARE_TU
 
+// lattice: 19 (D3Q19), 27 (D3Q27) or 127 (D3Q27h: D3Q27 with the complete Hermite basis)
 inline KernelInfo forward_kernel_for(int lattice, int storage, bool mask, bool two, bool field, bool tma,
                                      bool nearest) {
   const bool q19 = lattice == 19;
+  if (lattice == 127) {
+    switch (storage) {
+      case ST_F64: return forward_kernel_q127_s0(mask, two, field, tma, nearest);
+      case ST_F32: return forward_kernel_q127_s1(mask, two, field, tma, nearest);
+      case ST_F16: return forward_kernel_q127_s2(mask, two, field, tma, nearest);
+      case ST_BF16: return forward_kernel_q127_s3(mask, two, field, tma, nearest);
+    }
+    return KernelInfo{nullptr, 0, 0, 0, 0};
+  }
   switch (storage) {
     case ST_F64:
       return q19 ? forward_kernel_q19_s0(mask, two, field, tma, nearest) : forward_kernel_q27_s0(mask, two, field, tma, nearest);
@@ -128,6 +142,7 @@ inline KernelInfo forward_kernel_for(int lattice, int storage, bool mask, bool t
 }
 
 inline PopKernels pop_kernels_for(int lattice, int storage, bool mask, bool field) {
+  if (lattice == 127) return PopKernels{nullptr, nullptr, nullptr};  // second-order collision only
   const bool q19 = lattice == 19;
   switch (storage) {
     case ST_F64: return q19 ? pop_kernels_q19_s0(mask, field) : pop_kernels_q27_s0(mask, field);
@@ -138,6 +153,7 @@ inline PopKernels pop_kernels_for(int lattice, int storage, bool mask, bool fiel
 
 // adjoint kernel (FP64 and FP32 storage only; fn == nullptr otherwise)
 inline KernelInfo adjoint_kernel_for(int lattice, int storage, bool mask) {
+  if (lattice == 127) return KernelInfo{nullptr, 0, 0, 0, 0};  // the adjoint is of the second-order step
   const bool q19 = lattice == 19;
   switch (storage) {
     case ST_F64: return q19 ? adjoint_kernel_q19_s0(mask) : adjoint_kernel_q27_s0(mask);

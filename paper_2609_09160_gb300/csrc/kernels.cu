@@ -1,10 +1,10 @@
 // Kernel instantiations of one (lattice, storage) pair: the fused step in every force / mask / TMA
 // variant and, for FP64 and FP32 storage, its adjoint. The build compiles this file once per pair
-// with LBF_TU_LATTICE (19 or 27) and LBF_TU_STORAGE (0 FP64, 1 FP32, 2 FP16, 3 BF16) defined.
+// with LBF_TU_LATTICE (19, 27 or 127 = D3Q27h) and LBF_TU_STORAGE (0 FP64, 1 FP32, 2 FP16, 3 BF16) defined.
 #include "dispatch.cuh"
 
 #if !defined(LBF_TU_LATTICE) || !defined(LBF_TU_STORAGE)
-#error "compile kernels.cu with -DLBF_TU_LATTICE=19|27 -DLBF_TU_STORAGE=0..3"
+#error "compile kernels.cu with -DLBF_TU_LATTICE=19|27|127 -DLBF_TU_STORAGE=0..3"
 #endif
 
 namespace lbf {
@@ -13,8 +13,10 @@ namespace {
 using TuL = D3Q19;
 #elif LBF_TU_LATTICE == 27
 using TuL = D3Q27;
+#elif LBF_TU_LATTICE == 127
+using TuL = D3Q27H;
 #else
-#error "LBF_TU_LATTICE must be 19 or 27"
+#error "LBF_TU_LATTICE must be 19, 27 or 127"
 #endif
 #if LBF_TU_STORAGE == 0
 using TuS = double;
@@ -38,11 +40,17 @@ KernelInfo LBF_CAT(forward_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool ma
 }
 
 PopKernels LBF_CAT(pop_kernels_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask, bool field) {
+#if LBF_TU_LATTICE == 127
+  (void)mask;
+  (void)field;
+  return PopKernels{nullptr, nullptr, nullptr};  // the population kernels collide at second order
+#else
   return pop_kernels_ls<TuL, TuS>(mask, field);
+#endif
 }
 
 KernelInfo LBF_CAT(adjoint_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask) {
-#if LBF_TU_STORAGE <= 1
+#if LBF_TU_STORAGE <= 1 && LBF_TU_LATTICE != 127
   return mask ? adj_info<TuL, TuS, true>() : adj_info<TuL, TuS, false>();
 #else
   (void)mask;

@@ -29,7 +29,16 @@ struct D3Q27 {
            : (cx(q) * cx(q) + cy(q) * cy(q) + cz(q) * cz(q)) == 2 ? 1.0 / 54.0
                                                                    : 1.0 / 216.0;
   }
+  static constexpr bool HIGH = false;  // second-order Hermite truncation
   static constexpr const char* name = "D3Q27";
+};
+
+// D3Q27h (Sec. 2): the D3Q27 velocities with the complete Hermite basis; the post-collision
+// populations carry every Hermite coefficient the lattice supports, the higher ones reconstructed
+// from p*, u, N and F by the recursive closure
+struct D3Q27H : D3Q27 {
+  static constexpr bool HIGH = true;
+  static constexpr const char* name = "D3Q27H";
 };
 
 struct D3Q19 {
@@ -55,6 +64,7 @@ struct D3Q19 {
            : (cx(q) * cx(q) + cy(q) * cy(q) + cz(q) * cz(q)) == 1 ? 1.0 / 18.0
                                                                    : 1.0 / 36.0;
   }
+  static constexpr bool HIGH = false;
   static constexpr const char* name = "D3Q19";
 };
 

@@ -170,6 +170,105 @@ __device__ __forceinline__ void pop_pair(const PostColl<T>& P, T& fq, T& fo) {
   fo = s - d;
 }
 
+// ---------------------------------------------------------------------------------------------
+// D3Q27h (Sec. 2, complete Hermite basis with the recursive closure). For the multi-index
+// m = (mx, my, mz) in {0,1,2}^3 (how often each axis occurs in the tensor index) the
+// post-collision coefficient is
+//   P_m = u^m + (1 - omega) a_neq(m) + S_m / 2,   P_0 = p*,
+// with a_neq(m) = N for |m| = 2 and, for |m| >= 3, the sum over index pairs of N times the u's of
+// the other indices (the closure), and S_m / 2 the sum over index positions of h = F / (2 rho)
+// times the u's of the other indices (the Guo source to the same order). The basis functions are
+// h_mx(c_x) h_my(c_y) h_mz(c_z), h_0 = 1, h_1 = c, h_2 = c^2 - 1/3, normalised by
+// prod m_a! cs2^m_a, so f_q / w_q = sum_m H_m(c_q) P_m / norm_m is three one-axis contractions in
+// which the normalisation folds into the constants: per axis the value at c = 0 is
+// P_0 - 1.5 P_2 and at c = +/-1 it is P_0 + 3 P_2 +/- 3 P_1 (indices: the multiplicity of that
+// axis). Truncated at |m| <= 2 this is the second-order post_collision / pop_pair above.
+struct FullIdx {
+  int n;
+  int a[6];
+};
+__host__ __device__ constexpr FullIdx full_axes(int mx, int my, int mz) {
+  FullIdx r{0, {0, 0, 0, 0, 0, 0}};
+  for (int k = 0; k < mx; ++k) r.a[r.n++] = 0;
+  for (int k = 0; k < my; ++k) r.a[r.n++] = 1;
+  for (int k = 0; k < mz; ++k) r.a[r.n++] = 2;
+  return r;
+}
+
+template <int MX, int MY, int MZ, class T>
+__device__ __forceinline__ T full_coef(T p, const T (&u)[3], const T (&h)[3], const T (&Nt)[3][3], T omm) {
+  constexpr FullIdx I = full_axes(MX, MY, MZ);
+  constexpr int n = I.n;
+  if constexpr (n == 0) {
+    return p;
+  } else {
+    T eq = u[I.a[0]];
+#pragma unroll
+    for (int k = 1; k < n; ++k) eq *= u[I.a[k]];
+    T neq = T(0);
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+#pragma unroll
+      for (int j = i + 1; j < n; ++j) {
+        T t = Nt[I.a[i]][I.a[j]];
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+          if (k != i && k != j) t *= u[I.a[k]];
+        neq += t;
+      }
+    T src = T(0);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      T t = h[I.a[i]];
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+        if (k != i) t *= u[I.a[k]];
+      src += t;
+    }
+    return eq + omm * neq + src;
+  }
+}
+
+// f_q / w_q of all 27 directions in cube order, q = 9 (c_z + 1) + 3 (c_y + 1) + (c_x + 1)
+template <class T>
+__device__ __forceinline__ void full_populations(T p, const T (&u)[3], const T (&h)[3], const T (&Nt)[3][3], T omm,
+                                                 T (&g)[27]) {
+  T C[3][3][3];  // [mz][my][mx]
+  static_for<27>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    C[k / 9][(k / 3) % 3][k % 3] = full_coef<k % 3, (k / 3) % 3, k / 9, T>(p, u, h, Nt, omm);
+  });
+  T X[3][3][3];  // [mz][my][cx + 1]
+#pragma unroll
+  for (int mz = 0; mz < 3; ++mz)
+#pragma unroll
+    for (int my = 0; my < 3; ++my) {
+      const T e = C[mz][my][0] + T(3) * C[mz][my][2];
+      X[mz][my][1] = C[mz][my][0] - T(1.5) * C[mz][my][2];
+      X[mz][my][2] = e + T(3) * C[mz][my][1];
+      X[mz][my][0] = e - T(3) * C[mz][my][1];
+    }
+  T Y[3][3][3];  // [mz][cy + 1][cx + 1]
+#pragma unroll
+  for (int mz = 0; mz < 3; ++mz)
+#pragma unroll
+    for (int cx = 0; cx < 3; ++cx) {
+      const T e = X[mz][0][cx] + T(3) * X[mz][2][cx];
+      Y[mz][1][cx] = X[mz][0][cx] - T(1.5) * X[mz][2][cx];
+      Y[mz][2][cx] = e + T(3) * X[mz][1][cx];
+      Y[mz][0][cx] = e - T(3) * X[mz][1][cx];
+    }
+#pragma unroll
+  for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+    for (int cx = 0; cx < 3; ++cx) {
+      const T e = Y[0][cy][cx] + T(3) * Y[2][cy][cx];
+      g[9 + 3 * cy + cx] = Y[0][cy][cx] - T(1.5) * Y[2][cy][cx];
+      g[18 + 3 * cy + cx] = e + T(3) * Y[1][cy][cx];
+      g[3 * cy + cx] = e - T(3) * Y[1][cy][cx];
+    }
+}
+
 // new raw moments accumulated from pulled populations, pairwise
 template <class T>
 struct Accum {
@@ -422,12 +521,23 @@ struct SiteExtra {
 #ifndef LBF_FWD_MINB_Q27_16_NM
 #define LBF_FWD_MINB_Q27_16_NM 3
 #endif
-constexpr int fwd_rows(int Q, int bytes, bool mask = true) {
+// two-component D3Q19 FP32 (the droplet workload) has its own tile height: its per-site inputs
+// (phase field, two force vectors) need more registers than the single-component kernel, and
+// 7-row tiles (up to 72 registers at 3 CTAs/SM) remove the spills of 8-row ones (+2% at 128^3)
+#ifndef LBF_FWD_ROWS_Q19_TWO
+#define LBF_FWD_ROWS_Q19_TWO 7
+#endif
+#ifndef LBF_FWD_MINB_Q19_TWO
+#define LBF_FWD_MINB_Q19_TWO 3
+#endif
+constexpr int fwd_rows(int Q, int bytes, bool mask = true, bool two = false) {
+  if (two && Q == 19 && bytes == 4) return LBF_FWD_ROWS_Q19_TWO;
   return bytes == 8 ? LBF_FWD_ROWS_F64
                     : (bytes == 4 ? (Q == 19 ? LBF_FWD_ROWS_Q19 : (mask ? LBF_FWD_ROWS_Q27 : LBF_FWD_ROWS_Q27_NM))
                                   : (Q == 19 ? LBF_FWD_ROWS_Q19_16 : (mask ? LBF_FWD_ROWS_Q27_16 : LBF_FWD_ROWS_Q27_16_NM)));
 }
-constexpr int fwd_minb(int Q, int bytes, bool mask = true) {
+constexpr int fwd_minb(int Q, int bytes, bool mask = true, bool two = false) {
+  if (two && Q == 19 && bytes == 4) return LBF_FWD_MINB_Q19_TWO;
   return bytes == 8 ? 1
                     : (bytes == 4 ? (Q == 19 ? LBF_FWD_MINB_Q19 : (mask ? LBF_FWD_MINB_Q27 : LBF_FWD_MINB_Q27_NM))
                                   : (Q == 19 ? LBF_FWD_MINB_Q19_16 : (mask ? LBF_FWD_MINB_Q27_16 : LBF_FWD_MINB_Q27_16_NM)));
@@ -450,7 +560,7 @@ constexpr uint32_t kWaitPolls = 1u << 20;  // bound of every mbarrier wait
 #endif
 
 template <class L, class S, int BY, bool MASK, bool TWO, bool FF, bool TMA, bool RN>
-__global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeof(S)), MASK))
+__global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeof(S)), MASK, TWO))
     k_stream_collide(const FwdParams a, const __grid_constant__ CUtensorMap tmap) {
   using T = typename ComputeOf<S>::type;
   using D = Dirs<L>;
@@ -641,8 +751,6 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     }
     const T Fs0 = SITEF ? e.F[0] : Fu0, Fs1 = SITEF ? e.F[1] : Fu1, Fs2 = SITEF ? e.F[2] : Fu2;
     if constexpr (Codec<S>::scaled) omm *= a.sc.dec[2];  // N is in storage units (read_raw)
-    const PostColl<T> P =
-        post_collision<T>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9], Fs0, Fs1, Fs2, inv2rho, omm);
     T* w0 = ring + R::base(0) + (R::NS0 == 2 ? par : 0) * G0 + me;
     T* w1 = ring + R::base(1) + par * G1 + me;
     T* w2 = ring + R::base(2) + g2 + me;
@@ -659,18 +767,36 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
         b[D::gidx(q) * SITES] = v;
       }
     };
-    static_for<Q>([&](auto qc) {
-      constexpr int q = decltype(qc)::value;
-      constexpr bool need_q = H == 0 || L::cy(q) == H, need_o = H == 0 || L::cy(L::opp(q)) == H;
-      if constexpr (q == QREST) {
-        if constexpr (H == 0) rest_new = P.q0;
-      } else if constexpr (q < L::opp(q) && (need_q || need_o)) {
-        T fq, fo;
-        pop_pair<L, q, T>(P, fq, fo);
-        if constexpr (need_q) put(qc, fq);
-        if constexpr (need_o) put(std::integral_constant<int, L::opp(q)>{}, fo);
-      }
-    });
+    if constexpr (L::HIGH) {
+      const T uv[3] = {m[1], m[2], m[3]};
+      const T hv[3] = {Fs0 * inv2rho, Fs1 * inv2rho, Fs2 * inv2rho};
+      const T Nt[3][3] = {{m[4], m[7], m[8]}, {m[7], m[5], m[9]}, {m[8], m[9], m[6]}};
+      T g[27];
+      full_populations<T>(m[0], uv, hv, Nt, omm, g);
+      static_for<Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        if constexpr (q == QREST) {
+          if constexpr (H == 0) rest_new = g[q];
+        } else if constexpr (H == 0 || L::cy(q) == H) {
+          put(qc, g[q]);
+        }
+      });
+    } else {
+      const PostColl<T> P = post_collision<T>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8], m[9], Fs0, Fs1,
+                                              Fs2, inv2rho, omm);
+      static_for<Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        constexpr bool need_q = H == 0 || L::cy(q) == H, need_o = H == 0 || L::cy(L::opp(q)) == H;
+        if constexpr (q == QREST) {
+          if constexpr (H == 0) rest_new = P.q0;
+        } else if constexpr (q < L::opp(q) && (need_q || need_o)) {
+          T fq, fo;
+          pop_pair<L, q, T>(P, fq, fo);
+          if constexpr (need_q) put(qc, fq);
+          if constexpr (need_o) put(std::integral_constant<int, L::opp(q)>{}, fo);
+        }
+      });
+    }
     if constexpr (MASK) msk[g2 / GS2 + me] = e.solid ? 1 : 0;
     sol_new = e.solid;
     return e.solid;
@@ -679,7 +805,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   // the reduced halo staging pays on D3Q27 (9 of 26 directions per halo row); on D3Q19 (5 of 18)
   // the extra code measured slower than staging every direction
   auto stage_row = [&](auto par_c, int p, int g2, const SiteExtra<T, TWO>& e) -> bool {
-    if constexpr (L::Q == 27) {
+    if constexpr (L::Q == 27 && !L::HIGH) {  // D3Q27h: one staging body (compile time)
       if (row == 0) return stage(par_c, std::integral_constant<int, 1>{}, p, g2, e);
       if (row == ROWS - 1) return stage(par_c, std::integral_constant<int, -1>{}, p, g2, e);
     }

@@ -24,7 +24,8 @@ def _dtype_code(dtype):
 class Solver:
     """Moment-represented LB solver on one GPU.
 
-    shape = (nz, ny, nx); lattice 19 or 27; storage 'f64' | 'f32' | 'f16' | 'bf16'.
+    shape = (nz, ny, nx); lattice 19, 27 or '27h' (= 127, D3Q27 with the complete Hermite basis);
+    storage 'f64' | 'f32' | 'f16' | 'bf16'.
     force: uniform 3-vector; force_field: CUDA tensor (3, nz, ny, nx) in the compute dtype
     (float64 for 'f64' storage, else float32), kept by reference; mask: bool/uint8 (nz, ny, nx),
     nonzero = solid. two_component: dict(rho_l, rho_h, tau_l, tau_h, sigma, width, diffusivity).
@@ -41,7 +42,8 @@ class Solver:
         self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         self.compute_dtype = torch.float64 if self.storage == _lbf.LBF_F64 else torch.float32
         p = _lbf.lbf_params()
-        p.lattice, p.nx, p.ny, p.nz, p.storage = int(lattice), nx, ny, nz, self.storage
+        lattice = _lbf.LBF_D3Q27H if str(lattice).lower() in ("27h", "d3q27h") else int(lattice)
+        p.lattice, p.nx, p.ny, p.nz, p.storage = lattice, nx, ny, nz, self.storage
         p.tau = float(tau)
         for a in range(3):
             p.force[a] = float(force[a])
