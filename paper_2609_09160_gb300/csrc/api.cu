@@ -102,7 +102,8 @@ lbf_status check_params(const lbf_params* p) {
 int grid_x(int nx) { return (nx + FwdTile<8>::XOUT - 1) / FwdTile<8>::XOUT; }
 int grid_y(int ny, int by) { return (ny + by - 1) / by; }
 int fwd_by(int lattice, int storage, bool mask, bool two) {
-  return fwd_rows(lattice == LBF_D3Q19 ? 19 : 27, int(storage_bytes(storage)), mask, two);
+  return fwd_rows_lattice(lattice == LBF_D3Q19 ? 19 : 27, int(storage_bytes(storage)), mask, two,
+                          lattice == LBF_D3Q27H);
 }
 int min_zchunk(int nz) { return std::min(8, nz); }
 

@@ -25,7 +25,7 @@ struct KernelInfo {
 
 template <class L, class S, bool MASK, bool TWO, bool FF, bool TMA, bool RN>
 KernelInfo fwd_info() {
-  constexpr int BY = fwd_rows(L::Q, int(sizeof(S)), MASK, TWO);
+  constexpr int BY = fwd_rows_lattice(L::Q, int(sizeof(S)), MASK, TWO, L::HIGH);
   KernelInfo k;
   k.fn = reinterpret_cast<const void*>(&k_stream_collide<L, S, BY, MASK, TWO, FF, TMA, RN>);
   k.smem = fwd_smem_bytes<L, S, BY, MASK, TMA>();

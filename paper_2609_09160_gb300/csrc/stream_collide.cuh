@@ -183,89 +183,58 @@ __device__ __forceinline__ void pop_pair(const PostColl<T>& P, T& fq, T& fo) {
 // which the normalisation folds into the constants: per axis the value at c = 0 is
 // P_0 - 1.5 P_2 and at c = +/-1 it is P_0 + 3 P_2 +/- 3 P_1 (indices: the multiplicity of that
 // axis). Truncated at |m| <= 2 this is the second-order post_collision / pop_pair above.
-struct FullIdx {
-  int n;
-  int a[6];
-};
-__host__ __device__ constexpr FullIdx full_axes(int mx, int my, int mz) {
-  FullIdx r{0, {0, 0, 0, 0, 0, 0}};
-  for (int k = 0; k < mx; ++k) r.a[r.n++] = 0;
-  for (int k = 0; k < my; ++k) r.a[r.n++] = 1;
-  for (int k = 0; k < mz; ++k) r.a[r.n++] = 2;
-  return r;
-}
-
-template <int MX, int MY, int MZ, class T>
-__device__ __forceinline__ T full_coef(T p, const T (&u)[3], const T (&h)[3], const T (&Nt)[3][3], T omm) {
-  constexpr FullIdx I = full_axes(MX, MY, MZ);
-  constexpr int n = I.n;
-  if constexpr (n == 0) {
-    return p;
-  } else {
-    T eq = u[I.a[0]];
-#pragma unroll
-    for (int k = 1; k < n; ++k) eq *= u[I.a[k]];
-    T neq = T(0);
-#pragma unroll
-    for (int i = 0; i < n; ++i)
-#pragma unroll
-      for (int j = i + 1; j < n; ++j) {
-        T t = Nt[I.a[i]][I.a[j]];
-#pragma unroll
-        for (int k = 0; k < n; ++k)
-          if (k != i && k != j) t *= u[I.a[k]];
-        neq += t;
-      }
-    T src = T(0);
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-      T t = h[I.a[i]];
-#pragma unroll
-      for (int k = 0; k < n; ++k)
-        if (k != i) t *= u[I.a[k]];
-      src += t;
-    }
-    return eq + omm * neq + src;
-  }
-}
-
-// f_q / w_q of all 27 directions in cube order, q = 9 (c_z + 1) + 3 (c_y + 1) + (c_x + 1)
+// The kernel evaluates this sum in the factorised form below instead of forming the 27 P_m.
+// f_q / w_q of all 27 directions in cube order, q = 9 (c_z + 1) + 3 (c_y + 1) + (c_x + 1).
+// Every part of sum_m H_m(c) P_m / norm_m factorises over the axes: with the per-axis series
+//   phi_a(c)   = sum_k h_k(c) u_a^k / norm_k = 1 + 3 c u_a + 4.5 (c^2 - 1/3) u_a^2
+//   sig_a(c)   = h_a d(phi_a)/du_a,   del_a(c) = d(phi_a)/du_a = 3 c + 9 (c^2 - 1/3) u_a,
+//   nu_a(c)    = (1/2) d2(phi_a)/du_a2 = 4.5 (c^2 - 1/3),
+// the equilibrium part is p* + phi_x phi_y phi_z - 1, the Guo part replaces one factor phi_a by
+// sig_a, and the closure part is sum_a N_aa nu_a (other phi) + sum_(a<b) N_ab del_a del_b phi_c
+// (the coefficients P_m above summed over the basis, regrouped by axis).
 template <class T>
 __device__ __forceinline__ void full_populations(T p, const T (&u)[3], const T (&h)[3], const T (&Nt)[3][3], T omm,
                                                  T (&g)[27]) {
-  T C[3][3][3];  // [mz][my][mx]
-  static_for<27>([&](auto kc) {
-    constexpr int k = decltype(kc)::value;
-    C[k / 9][(k / 3) % 3][k % 3] = full_coef<k % 3, (k / 3) % 3, k / 9, T>(p, u, h, Nt, omm);
-  });
-  T X[3][3][3];  // [mz][my][cx + 1]
+  // ps = phi - 1 (small): the equilibrium part p* + prod(1 + ps) - 1 is accumulated as
+  // ps_x + phi_x (ps_y + phi_y ps_z), so no O(1) term is ever cancelled (FP32 keeps the deviations)
+  T ph[3][3], ps[3][3], sg[3][3], dl[3][3];  // [axis][c + 1]
 #pragma unroll
-  for (int mz = 0; mz < 3; ++mz)
+  for (int a = 0; a < 3; ++a) {
+    const T u2 = u[a] * u[a];
+    ps[a][1] = T(-1.5) * u2;
+    const T e = T(3) * u2;
+    ps[a][2] = e + T(3) * u[a];
+    ps[a][0] = e - T(3) * u[a];
 #pragma unroll
-    for (int my = 0; my < 3; ++my) {
-      const T e = C[mz][my][0] + T(3) * C[mz][my][2];
-      X[mz][my][1] = C[mz][my][0] - T(1.5) * C[mz][my][2];
-      X[mz][my][2] = e + T(3) * C[mz][my][1];
-      X[mz][my][0] = e - T(3) * C[mz][my][1];
-    }
-  T Y[3][3][3];  // [mz][cy + 1][cx + 1]
-#pragma unroll
-  for (int mz = 0; mz < 3; ++mz)
-#pragma unroll
-    for (int cx = 0; cx < 3; ++cx) {
-      const T e = X[mz][0][cx] + T(3) * X[mz][2][cx];
-      Y[mz][1][cx] = X[mz][0][cx] - T(1.5) * X[mz][2][cx];
-      Y[mz][2][cx] = e + T(3) * X[mz][1][cx];
-      Y[mz][0][cx] = e - T(3) * X[mz][1][cx];
-    }
+    for (int c = 0; c < 3; ++c) ph[a][c] = T(1) + ps[a][c];
+    const T hu = T(6) * h[a] * u[a];  // 4.5 * (2/3) * 2 h u, and -1.5 * 2 h u = -hu / 2
+    sg[a][1] = T(-0.5) * hu;
+    sg[a][2] = hu + T(3) * h[a];
+    sg[a][0] = hu - T(3) * h[a];
+    dl[a][1] = T(-3) * u[a];
+    dl[a][2] = T(3) + T(6) * u[a];
+    dl[a][0] = T(-3) + T(6) * u[a];
+  }
+  const T nu0 = T(-1.5), nu1 = T(3);  // nu_a at c = 0 and c = +/-1
 #pragma unroll
   for (int cy = 0; cy < 3; ++cy)
 #pragma unroll
     for (int cx = 0; cx < 3; ++cx) {
-      const T e = Y[0][cy][cx] + T(3) * Y[2][cy][cx];
-      g[9 + 3 * cy + cx] = Y[0][cy][cx] - T(1.5) * Y[2][cy][cx];
-      g[18 + 3 * cy + cx] = e + T(3) * Y[1][cy][cx];
-      g[3 * cy + cx] = e - T(3) * Y[1][cy][cx];
+      const T nx = cx == 1 ? nu0 : nu1, ny = cy == 1 ? nu0 : nu1;
+      const T A = ph[0][cx] * ph[1][cy];
+      const T Exy = p + (ps[0][cx] + ph[0][cx] * ps[1][cy]);  // p* + phi_x phi_y - 1
+      const T Bs = sg[0][cx] * ph[1][cy] + ph[0][cx] * sg[1][cy];
+      const T Bn = Nt[0][0] * nx * ph[1][cy] + Nt[1][1] * ph[0][cx] * ny + Nt[0][1] * dl[0][cx] * dl[1][cy];
+      const T Dx = dl[0][cx] * ph[1][cy], Dy = ph[0][cx] * dl[1][cy];
+      const T An = Nt[2][2] * A;
+      const T Cn = Nt[0][2] * Dx + Nt[1][2] * Dy;
+#pragma unroll
+      for (int cz = 0; cz < 3; ++cz) {
+        const T nz = cz == 1 ? nu0 : nu1;
+        const T eqs = A * (ps[2][cz] + sg[2][cz]) + Bs * ph[2][cz];
+        const T neq = Bn * ph[2][cz] + An * nz + Cn * dl[2][cz];
+        g[9 * cz + 3 * cy + cx] = Exy + eqs + omm * neq;
+      }
     }
 }
 
@@ -535,6 +504,14 @@ constexpr int fwd_rows(int Q, int bytes, bool mask = true, bool two = false) {
   return bytes == 8 ? LBF_FWD_ROWS_F64
                     : (bytes == 4 ? (Q == 19 ? LBF_FWD_ROWS_Q19 : (mask ? LBF_FWD_ROWS_Q27 : LBF_FWD_ROWS_Q27_NM))
                                   : (Q == 19 ? LBF_FWD_ROWS_Q19_16 : (mask ? LBF_FWD_ROWS_Q27_16 : LBF_FWD_ROWS_Q27_16_NM)));
+}
+// D3Q27h with 16-bit storage and no walls: 6-row tiles (up to 80 registers at 3 CTAs/SM), as
+// the full-basis staging spills at the 72 registers of 7-row tiles
+#ifndef LBF_FWD_ROWS_Q27H_16_NM
+#define LBF_FWD_ROWS_Q27H_16_NM 6
+#endif
+constexpr int fwd_rows_lattice(int Q, int bytes, bool mask, bool two, bool high) {
+  return (high && bytes == 2 && !mask) ? LBF_FWD_ROWS_Q27H_16_NM : fwd_rows(Q, bytes, mask, two);
 }
 constexpr int fwd_minb(int Q, int bytes, bool mask = true, bool two = false) {
   if (two && Q == 19 && bytes == 4) return LBF_FWD_MINB_Q19_TWO;

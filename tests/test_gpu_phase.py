@@ -1,5 +1,6 @@
 """GPU parity of the two-component coupling (Allen-Cahn phase field + capillary force, equal
-densities) with the FP64 oracle, and exact per-component mass conservation."""
+densities) with the FP64 oracle on D3Q19, D3Q27 and D3Q27h, and exact per-component mass
+conservation."""
 import pytest
 import torch
 
@@ -11,11 +12,11 @@ from paper_2609_09160_gb300 import Solver
 from _helpers import TOL, group_errors, rel_max
 
 pytestmark = pytest.mark.gpu
-LAT = {19: oracle.D3Q19, 27: oracle.D3Q27}
+LAT = {19: oracle.D3Q19, 27: oracle.D3Q27, 127: oracle.D3Q27H}  # 127: D3Q27h
 TC = dict(rho_l=1.0, rho_h=1.0, tau_l=1.0, tau_h=0.8, sigma=0.03, width=4.0, diffusivity=0.1)
 
 
-@pytest.mark.parametrize("lattice", [19, 27])
+@pytest.mark.parametrize("lattice", [19, 27, 127])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_two_component_matches_oracle(lattice, storage):
     shape = (14, 17, 35)
