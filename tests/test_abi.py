@@ -86,6 +86,8 @@ def test_workspace_holds_two_moment_buffers(lib):
 
 @pytest.mark.parametrize("kw,status", [
     (dict(lattice=15), _lbf.LBF_EINVAL),
+    (dict(lattice=28), _lbf.LBF_EINVAL),
+    (dict(lattice=_lbf.LBF_D3Q27H, populations=1), _lbf.LBF_ENOTSUP),
     (dict(nx=0), _lbf.LBF_EINVAL),
     (dict(tau=0.5), _lbf.LBF_EINVAL),
     (dict(storage=7), _lbf.LBF_EINVAL),
@@ -107,6 +109,11 @@ def test_validation_rejects_bad_parameters(lib, kw, status):
 
 def test_valid_parameters(lib):
     assert _lbf.lbf_validate(params()) == _lbf.LBF_OK
+    for lattice in (_lbf.LBF_D3Q19, _lbf.LBF_D3Q27, _lbf.LBF_D3Q27H):
+        for storage in (_lbf.LBF_F64, _lbf.LBF_F32, _lbf.LBF_F16, _lbf.LBF_BF16):
+            assert _lbf.lbf_validate(params(lattice=lattice, storage=storage)) == _lbf.LBF_OK
+    # D3Q27h keeps the 10-field state: same workspace as D3Q27
+    assert _lbf.lbf_workspace_bytes(params(lattice=_lbf.LBF_D3Q27H)) == _lbf.lbf_workspace_bytes(params(lattice=27))
     tc = params(two_component=1, tau_l=1.0, tau_h=0.8, rho_l=1.0, rho_h=1.0, width=4.0, sigma=0.03, diffusivity=0.1)
     assert _lbf.lbf_validate(tc) == _lbf.LBF_OK
 
