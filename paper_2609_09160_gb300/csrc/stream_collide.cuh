@@ -216,25 +216,24 @@ __device__ __forceinline__ void full_populations(T p, const T (&u)[3], const T (
     dl[a][0] = T(-3) + T(6) * u[a];
   }
   const T nu0 = T(-1.5), nu1 = T(3);  // nu_a at c = 0 and c = +/-1
+  // per (c_x, c_y) column the 27 values are g = K0 + K1 ps_z + K2 sig_z + K3 nu_z + K4 del_z
+  const T nxx0 = Nt[0][0] * nu0, nxx1 = Nt[0][0] * nu1, nyy0 = Nt[1][1] * nu0, nyy1 = Nt[1][1] * nu1;
+  const T oz = omm * Nt[2][2];
 #pragma unroll
   for (int cy = 0; cy < 3; ++cy)
 #pragma unroll
     for (int cx = 0; cx < 3; ++cx) {
-      const T nx = cx == 1 ? nu0 : nu1, ny = cy == 1 ? nu0 : nu1;
       const T A = ph[0][cx] * ph[1][cy];
       const T Exy = p + (ps[0][cx] + ph[0][cx] * ps[1][cy]);  // p* + phi_x phi_y - 1
       const T Bs = sg[0][cx] * ph[1][cy] + ph[0][cx] * sg[1][cy];
-      const T Bn = Nt[0][0] * nx * ph[1][cy] + Nt[1][1] * ph[0][cx] * ny + Nt[0][1] * dl[0][cx] * dl[1][cy];
-      const T Dx = dl[0][cx] * ph[1][cy], Dy = ph[0][cx] * dl[1][cy];
-      const T An = Nt[2][2] * A;
-      const T Cn = Nt[0][2] * Dx + Nt[1][2] * Dy;
+      const T Bn = (cx == 1 ? nxx0 : nxx1) * ph[1][cy] + (cy == 1 ? nyy0 : nyy1) * ph[0][cx] +
+                   Nt[0][1] * (dl[0][cx] * dl[1][cy]);
+      const T t = Bs + omm * Bn;
+      const T K0 = Exy + t, K1 = A + t, K3 = oz * A;
+      const T K4 = omm * (Nt[0][2] * (dl[0][cx] * ph[1][cy]) + Nt[1][2] * (ph[0][cx] * dl[1][cy]));
 #pragma unroll
-      for (int cz = 0; cz < 3; ++cz) {
-        const T nz = cz == 1 ? nu0 : nu1;
-        const T eqs = A * (ps[2][cz] + sg[2][cz]) + Bs * ph[2][cz];
-        const T neq = Bn * ph[2][cz] + An * nz + Cn * dl[2][cz];
-        g[9 * cz + 3 * cy + cx] = Exy + eqs + omm * neq;
-      }
+      for (int cz = 0; cz < 3; ++cz)
+        g[9 * cz + 3 * cy + cx] = K0 + K1 * ps[2][cz] + A * sg[2][cz] + K3 * (cz == 1 ? nu0 : nu1) + K4 * dl[2][cz];
     }
 }
 
