@@ -301,7 +301,8 @@ def cpu_baseline_oracle(target_seconds=12.0, shape=(4, 256, 256), max_steps=50):
 
 
 def extras(torch, device, quick):
-    """Secondary rows: D3Q27 512^3 storage dtypes, D3Q19 512^3, two-component, FP64, adjoint ratio."""
+    """Secondary rows: D3Q27, D3Q19 and D3Q27h 512^3 in every storage dtype, the population-form
+    channel, two-component, FP64, adjoint ratio."""
     import synth
     from paper_2609_09160_gb300 import Solver, rollout
 
