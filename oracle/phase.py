@@ -16,7 +16,16 @@ TEST INFRASTRUCTURE (oracle).
   advective form for a divergence-free u and keeps sum(phi) exact on a periodic box.
 * Chemical potential mu = 4 beta phi (phi - 1)(phi - 1/2) - kappa lap phi, beta = 12 sigma / W,
   kappa = 3 sigma W / 2; capillary force F_s = mu grad phi.
-* The pressure and viscosity-gradient forces vanish when rho_L = rho_H; only that case is built.
+* Density contrast (Sec. 2, force split F = F_s + F_b + F_p + F_nu):
+    F_p  = -p* cs2 grad rho                                          (as printed)
+    F_nu = nu S . grad rho,  S = -(omega / cs2) a*_neq               (reading: the printed
+           coefficient "nu omega cs2 a*_neq" is dimensionally garbled; this is the viscous stress
+           nu (grad u + grad u^T) . grad rho that the per-unit-mass LB step leaves out, with the
+           Chapman-Enskog strain rate of the raw, uncorrected second moments a*_neq = a*2 - a*1 a*1)
+  Both vanish when rho_L = rho_H. F_b may be given as a body acceleration a (F_b = rho(phi) a).
+* Walls (solid mask): halfway bounce-back for the populations; the phase field is not advanced at
+  solid sites (they keep their phi, u = 0 there), so a wall in contact with a single bulk phase
+  exchanges no phi. Wetting (a contact line on a wall) is not modelled.
 """
 import torch
 
@@ -89,24 +98,49 @@ def omega(phi, tau_l, tau_h):
     return 1.0 / (nu / CS2 + 0.5)
 
 
-def total_force(phi, p, body, sigma, W):
-    """F = F_s + F_b (F_p and F_nu are zero at equal densities)."""
-    F = capillary_force(phi, sigma, W)
-    return F + lbm.as_field(body, phi.shape)
+def pressure_force(phi, p, rho_l, rho_h):
+    """F_p = -p* cs2 grad rho, grad rho = (rho_H - rho_L) grad phi (Sec. 2)."""
+    return -(CS2 * p).unsqueeze(0) * ((rho_h - rho_l) * gradient(phi))
+
+
+def viscous_force(phi, a2neq, tau_l, tau_h, rho_l, rho_h):
+    """F_nu_a = nu S_ab d_b rho with S = -(omega / cs2) a*_neq (reading of Sec. 2, see header)."""
+    nu = CS2 * (tau_l - 0.5) + phi * (CS2 * (tau_h - tau_l))
+    coef = -(nu * omega(phi, tau_l, tau_h) / CS2)
+    grho = (rho_h - rho_l) * gradient(phi)
+    return coef.unsqueeze(0) * torch.einsum("ab...,b...->a...", a2neq, grho)
+
+
+def total_force(phi, p, body, sigma, W, a2neq=None, rho_l=1.0, rho_h=1.0, tau_l=1.0, tau_h=1.0,
+                body_accel=None):
+    """F = F_s + F_b + F_p + F_nu (F_p and F_nu only with a density contrast). body is a force per
+    unit volume; body_accel, if given, adds rho(phi) a."""
+    F = capillary_force(phi, sigma, W) + lbm.as_field(body, phi.shape)
+    if body_accel is not None:
+        F = F + density(phi, rho_l, rho_h).unsqueeze(0) * lbm.as_field(body_accel, phi.shape)
+    if rho_l != rho_h:
+        F = F + pressure_force(phi, p, rho_l, rho_h) + viscous_force(phi, a2neq, tau_l, tau_h, rho_l, rho_h)
+    return F
 
 
 def run(lat, M0, phi0, steps, tau_l, tau_h, sigma, W, D, rho_l=1.0, rho_h=1.0,
-        body=(0.0, 0.0, 0.0), callback=None):
-    """Two-component run on a periodic box. State (populations f, phi). Order of one step:
+        body=(0.0, 0.0, 0.0), callback=None, solid=None, body_accel=None):
+    """Two-component run. State (populations f, phi). Order of one step:
     phi^{n+1} = AC(phi^n, u^n); collide with F^n, rho(phi^n), omega(phi^n) and stream;
-    F^{n+1} = F_s(phi^{n+1}) + F_b is the force of the new state (Eq. corr at t+1).
+    F^{n+1} = F(phi^{n+1}, p*^{n+1}, a*_neq^{n+1}) is the force of the new state (Eq. corr at t+1),
+    with p* and a*_neq taken from the raw moments of the streamed populations. F^0 uses the
+    non-equilibrium part N = A - u u of the initial state.
+    solid: bool (nz, ny, nx) or None (see the header for walls). Solid sites keep M0 and phi0.
     Returns (M, phi) after `steps` steps; callback(t, M, phi) after each step."""
-    if rho_l != rho_h:
-        raise NotImplementedError("density contrast needs the pressure and viscous forces")
     M0 = torch.as_tensor(M0, dtype=torch.float64)
     phi = torch.as_tensor(phi0, dtype=torch.float64).clone()
     shape = phi.shape
-    F = total_force(phi, M0[0], body, sigma, W)
+    if solid is not None:
+        solid = torch.as_tensor(solid, dtype=torch.bool)
+    kw = dict(rho_l=rho_l, rho_h=rho_h, tau_l=tau_l, tau_h=tau_h, body_accel=body_accel)
+    p0, u0, A0 = lbm.unpack(M0)
+    N0 = A0 - torch.einsum("a...,b...->ab...", u0, u0)
+    F = total_force(phi, p0, body, sigma, W, a2neq=N0, **kw)
     rho = density(phi, rho_l, rho_h)
     f = lbm.populations_from_moments(lat, M0, F, rho)
     M = M0
@@ -114,12 +148,19 @@ def run(lat, M0, phi0, steps, tau_l, tau_h, sigma, W, D, rho_l=1.0, rho_h=1.0,
         rho = density(phi, rho_l, rho_h)
         om = omega(phi, tau_l, tau_h)
         _, u, _ = lbm.macroscopic(lat, f, F, rho)
+        if solid is not None:
+            u = torch.where(solid.unsqueeze(0), torch.zeros_like(u), u)
         phi_new = allen_cahn_step(phi, u, D, W)
-        f = lbm.step(lat, f, F, rho, om)
+        if solid is not None:
+            phi_new = torch.where(solid, phi, phi_new)
+        f = lbm.step(lat, f, F, rho, om, solid)
         phi = phi_new
-        F = total_force(phi, None, body, sigma, W)
+        a0, a1, a2 = lbm.hermite_project(lat, f)
+        F = total_force(phi, a0, body, sigma, W, a2neq=a2 - torch.einsum("a...,b...->ab...", a1, a1), **kw)
         if callback is not None or t == steps:
             M = lbm.moments_from_populations(lat, f, F, density(phi, rho_l, rho_h))
+            if solid is not None:
+                M = torch.where(solid.unsqueeze(0), M0, M)
             if callback is not None:
                 callback(t, M, phi)
     return M, phi
