@@ -143,6 +143,10 @@ def gpu_identifier(torch, dev):
 
 
 LATTICE_NAME = {19: "D3Q19", 27: "D3Q27", 127: "D3Q27h"}
+# FP32 bytes per site of a two-component step beyond the 80 B of the moments, over its three
+# kernels: the fused step reads phi and F at t and t+1 (4 + 12 + 4 + 12), the phase-field advance
+# reads phi, u, G and writes phi (4 + 12 + 12 + 4), the forces read phi and write F and G (4 + 24)
+TWO_COMPONENT_EXTRA_BYTES = 32 + 32 + 28
 
 WORKLOADS = {
     # key: (lattice, storage, builder) -- the headline is "channel256"
@@ -342,7 +346,7 @@ def extras(torch, device, quick):
     # two-component droplet, 128^3, R = 20, equal densities, tau = 1 (config of the Laplace test)
     s, M0, _ = droplet_solver(torch, device)
     s.set_moments(M0, s._phi0)
-    r = rate(s, 50 if quick else 200, 5, algorithmic_bytes("f32") + 4 * (1 + 1 + 3 + 3) + 4 * 3 * 2)
+    r = rate(s, 50 if quick else 200, 5, TWO_COMPONENT_EXTRA_BYTES + algorithmic_bytes("f32"))
     r["note"] = "3 kernels per step (phase field advance, forces, fused LB)"
     out["droplet128_d3q19_f32"] = r
     del s, M0
@@ -429,7 +433,7 @@ def run_ours(args):
     lattice, storage, kind = WORKLOADS[args.workload]
     bpl = algorithmic_bytes(storage, mask=(kind == "channel"))
     if kind == "droplet":
-        bpl += 4 * (1 + 1 + 3 + 3) + 4 * 3 * 2
+        bpl += TWO_COMPONENT_EXTRA_BYTES
     t_launch = t / args.steps
     achieved = bpl * n / t_launch / 1e9
     traffic = ncu_traffic(args.workload)
