@@ -176,3 +176,27 @@ def test_planted_mistake_in_laplacian_factor_is_caught(monkeypatch):
     k = 2 * math.pi / n
     psi = torch.sin(k * x).expand(1, 1, n)
     assert (phase.laplacian(psi) + 4 * math.sin(k / 2) ** 2 * psi).abs().max() > 1e-4
+
+
+def _pressure_force_dropped(phi, p, rho_l, rho_h):
+    return torch.zeros((3,) + tuple(phi.shape), dtype=torch.float64)
+
+
+def _pressure_force_sign(phi, p, rho_l, rho_h):
+    return (CS2 * p).unsqueeze(0) * ((rho_h - rho_l) * phase.gradient(phi))
+
+
+def _pressure_force_no_cs2(phi, p, rho_l, rho_h):
+    return -p.unsqueeze(0) * ((rho_h - rho_l) * phase.gradient(phi))
+
+
+@pytest.mark.parametrize("mutant", [_pressure_force_dropped, _pressure_force_sign, _pressure_force_no_cs2],
+                         ids=["dropped", "sign", "no_cs2"])
+def test_planted_mistake_in_pressure_force_is_caught(mutant, monkeypatch):
+    """F_p = -p* cs2 grad rho (Sec. 2): dropping it, flipping its sign or losing the cs2 breaks the
+    rest state of a density interface at uniform physical pressure."""
+    from test_oracle_pressure_force import pressure_pin_holds
+
+    assert pressure_pin_holds()
+    monkeypatch.setattr(phase, "pressure_force", mutant)
+    assert not pressure_pin_holds()
