@@ -110,15 +110,19 @@ typedef struct {
 } lbf_params;
 
 /* Workspace bytes the context needs for these parameters, 0 if the parameters are invalid.
-   Host-only: makes no CUDA call. The moment buffers take 2 * 10 * nx*ny*nz * sizeof(storage). */
+   Host-only: makes no CUDA call. The moment buffers take 2 * 10 * nx*ny*nz * sizeof(storage).
+   Paper: Sec. 3 memory model (10 moment fields per site, flip/flop buffers). */
 size_t lbf_workspace_bytes(const lbf_params* params);
 
-/* Checks parameters on the host without touching the GPU. */
+/* Checks parameters on the host without touching the GPU.
+   Paper: Sec. 2 (the lattices; tau > 1/2 from nu = cs2 (tau - 1/2) under Eq. pullLB). */
 lbf_status lbf_validate(const lbf_params* params);
 
 /* Creates a context on the current CUDA device. workspace: DEVICE pointer, 256-byte aligned, at
    least lbf_workspace_bytes(params) bytes, owned by the caller and kept alive until lbf_destroy.
-   The state is zero (fluid at rest) until lbf_set_moments. */
+   The state is zero (fluid at rest) until lbf_set_moments.
+   Paper: Sec. 2 statement of the problem (lattice, domain, tau, walls, body force F^b, phase-field
+   parameters of Eq. ACeq) and Sec. 3 (flip/flop moment buffers). */
 lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, size_t bytes);
 
 /* Loads the public state. src: 10 fields (public layout) of dtype LBF_F64 or LBF_F32, HOST or
@@ -126,38 +130,54 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
    required when two_component, else ignored. Host sources are copied through a staging area of
    the workspace; pinned host memory makes the copies asynchronous. For 16-bit storage the
    power-of-two scales are chosen here (unless scale_hint is set). Also computes the initial
-   phase-field force when two_component. */
+   phase-field force when two_component.
+   Paper: Sec. 2, the velocity-pressure Hermite coefficients a(0) = p*, a(1) = u, a(2) of
+   Eqs. reqtfeq, hermite_teq; the capillary force F^s = mu grad phi of the force split. */
 lbf_status lbf_set_moments(lbf_ctx* ctx, const void* src, int src_dtype, const void* phi);
 
 /* Advances n >= 0 time steps (one fused kernel per step; two more phase-field kernels per step
    when two_component). The conservation sums of the final state are computed on the last step.
-   Returns LBF_EUNSTABLE if an earlier lbf_reduce/lbf_synchronize saw the instability flag. */
+   Returns LBF_EUNSTABLE if an earlier lbf_reduce/lbf_synchronize saw the instability flag.
+   Paper: Eq. (pullLLB) followed by Eq. (corr), Sec. 2; with two_component also Eq. (ACeq) by FTCS
+   and the force split F = F^s + F^b (Sec. 2). */
 lbf_status lbf_step(lbf_ctx* ctx, int n);
 
 /* Writes the public state (dst, 10 fields) and, when two_component and phi_dst != NULL, the phase
    field, in dtype LBF_F64 or LBF_F32, to HOST or DEVICE memory (detected). Asynchronous for device
-   or pinned host destinations. */
+   or pinned host destinations.
+   Paper: Sec. 2, the velocity-pressure Hermite coefficients (p*, u, a(2)) after Eq. (corr). */
 lbf_status lbf_moments(lbf_ctx* ctx, void* dst, int dst_dtype, void* phi_dst);
 
 /* Waits for the stream and returns FP64 [sum p*, sum ux, sum uy, sum uz, sum phi, sum u.u] over
    fluid sites of the current state (out: HOST, 6 doubles). LBF_EUNSTABLE if any step so far saw a
-   non-finite value or |u|^2 > 0.16 (out is still filled). */
+   non-finite value or |u|^2 > 0.16 (out is still filled).
+   Paper: Sec. 4, the kinetic-energy diagnostic E(t) of the Taylor-Green test (sum u.u), and the
+   totals that Eq. (pullLLB) conserves (sum p*, sum u without force, sum phi of Eq. ACeq). */
 lbf_status lbf_reduce(lbf_ctx* ctx, double* out);
 
-/* Waits for the stream; LBF_EUNSTABLE as for lbf_reduce. */
+/* Waits for the stream; LBF_EUNSTABLE as for lbf_reduce; LBF_EINTERNAL if a step was abandoned
+   (a bounded TMA wait gave up, or an index check of the LBF_DEBUG build failed).
+   Paper: no counterpart (stream completion and the library's instability check). */
 lbf_status lbf_synchronize(lbf_ctx* ctx);
 
-/* Bytes of one internal state buffer (10 * nx*ny*nz * sizeof(storage)). */
+/* Bytes of one internal state buffer (10 * nx*ny*nz * sizeof(storage)).
+   Paper: Sec. 3 memory model (10 fields per site). */
 size_t lbf_state_bytes(const lbf_ctx* ctx);
 
-/* Copies the current internal state to / from a caller DEVICE buffer of lbf_state_bytes()
-   (checkpointing; stream-ordered). */
+/* Copies the current internal state to a caller DEVICE buffer of lbf_state_bytes()
+   (checkpointing; stream-ordered).
+   Paper: no counterpart (checkpoints of the Sec. 3 moment buffers). */
 lbf_status lbf_copy_state(lbf_ctx* ctx, void* dst);
+
+/* Loads the current internal state from a caller DEVICE buffer of lbf_state_bytes() (restart;
+   stream-ordered).
+   Paper: no counterpart (checkpoints of the Sec. 3 moment buffers). */
 lbf_status lbf_load_state(lbf_ctx* ctx, const void* src);
 
 /* One single-component step from internal state src to internal state dst (caller DEVICE
    buffers of lbf_state_bytes(); src != dst). The context's own state is not touched. Solid
-   sites of dst are not written. */
+   sites of dst are not written. A src that is not 16-byte aligned is read without TMA.
+   Paper: Eq. (pullLLB) followed by Eq. (corr), Sec. 2. */
 lbf_status lbf_step_state(lbf_ctx* ctx, const void* src, void* dst);
 
 /* Adjoint of one single-component step (not in the paper; the discrete adjoint of the step
@@ -166,7 +186,8 @@ lbf_status lbf_step_state(lbf_ctx* ctx, const void* src, void* dst);
    lambda_out = dL/dM(t) (same layout and dtype, DEVICE, distinct from lambda_in) and adds
    dL/dF contributed by this step to grad_force (DEVICE, FP64, [3][nz][ny][nx]) for the total
    per-site force (uniform force + force_field). Solid sites pass lambda through unchanged and
-   get no force gradient. Not available for 16-bit storage or two_component (LBF_ENOTSUP). */
+   get no force gradient. Not available for 16-bit storage or two_component (LBF_ENOTSUP).
+   Paper: no counterpart (the exact transpose of the linearised Eq. (pullLLB) + Eq. (corr)). */
 lbf_status lbf_adjoint_step(lbf_ctx* ctx, const void* state_t, const void* state_t1, const void* lambda_in,
                             void* lambda_out, double* grad_force);
 
@@ -179,24 +200,41 @@ lbf_status lbf_adjoint_step(lbf_ctx* ctx, const void* state_t, const void* state
    as for lbf_create; params->mask and the two-component fields are not used.
    src, dst: caller DEVICE buffers of 10*nx*ny*nz values in the internal state layout (the bytes
    lbf_copy_state produces; for FP32/FP64 storage the tensor fields hold a2 - u u), src != dst.
+   A src that is 16-byte aligned (and whose rows are a multiple of 16 bytes) is staged with TMA;
+   any other src is read by the kernel variant that loads every site directly.
    mask_device: optional DEVICE mask, nx*ny*nz bytes, nonzero = solid (solid sites of dst are not
    written). sums_device: optional DEVICE output of 6 doubles, the sums of lbf_reduce for dst.
+   flags_device: optional DEVICE output of one unsigned word, written after the step: 0 = the step
+   completed; bit 0 = a non-finite value or |u|^2 > 0.16 was stored (unstable); bit 1 = a TMA plane
+   load did not complete in time and bit 2 = a TMA stage was misaligned (in both cases the step was
+   abandoned and dst is incomplete); bit 3 = an index check of the LBF_DEBUG build failed.
    The library keeps the per-block partial sums, a block counter and the error flags in one static
    device array of 1 MiB + 256 bytes per GPU that loads it (held until the process exits), enough
-   for 16384 CTAs: ceil(nx/30) * ceil(ny/8) (FP32; ny/4 for FP64) must not exceed 16384, else
-   LBF_EINVAL. The first call on a device looks up that array's device address; make it before any
-   stream capture. Every call clears the counter and flags it needs (cudaMemsetAsync, which does not
+   for 16384 CTAs: ceil(nx/30) * ceil(ny/R) must not exceed 16384, else LBF_EINVAL, where R is the
+   number of output rows per CTA of the kernel the parameters select (FP32: 8 for D3Q19 and for
+   D3Q27/D3Q27H with a mask, 6 for D3Q27/D3Q27H without one; FP64: 4); the error message names R.
+   The first call on a device looks up that array's device address; make it before any stream
+   capture. Every call clears the counter and flags it needs (cudaMemsetAsync, which does not
    allocate). All calls share the array: calls that can overlap on the GPU (other streams, other
-   host threads) race on it; calls ordered on one stream are safe. Instability is not reported
-   (no context to hold it); the u.u sum shows it. Asynchronous on params->stream. */
+   host threads) race on it; calls ordered on one stream are safe. Asynchronous on params->stream.
+   Paper: no counterpart; it runs the step of Eq. (pullLLB) + Eq. (corr), Sec. 2. */
 lbf_status lbf_step_static(const lbf_params* params, const void* src, void* dst, const uint8_t* mask_device,
-                           double* sums_device);
+                           double* sums_device, unsigned* flags_device);
 
-/* Releases the host-side context. The workspace stays owned by the caller. */
+/* Releases the host-side context. The workspace stays owned by the caller.
+   Paper: no counterpart. */
 lbf_status lbf_destroy(lbf_ctx* ctx);
 
+/* Name of a status code ("LBF_OK", ...), a static string.
+   Paper: no counterpart. */
 const char* lbf_status_string(int status);
+
+/* Message of the last error on the calling thread (empty if none), valid until the next call.
+   Paper: no counterpart. */
 const char* lbf_last_error(void);
+
+/* ABI version of this library.
+   Paper: no counterpart. */
 int lbf_version(void);
 
 #ifdef __cplusplus

@@ -65,7 +65,7 @@ def load_library(path=LIB_PATH):
         "lbf_load_state": (I, [VP, VP]),
         "lbf_step_state": (I, [VP, VP, VP]),
         "lbf_adjoint_step": (I, [VP, VP, VP, VP, VP, VP]),
-        "lbf_step_static": (I, [P(lbf_params), VP, VP, VP, VP]),
+        "lbf_step_static": (I, [P(lbf_params), VP, VP, VP, VP, VP]),
         "lbf_destroy": (I, [VP]),
         "lbf_status_string": (ctypes.c_char_p, [I]),
         "lbf_last_error": (ctypes.c_char_p, []),
@@ -147,10 +147,11 @@ def lbf_adjoint_step(ctx, state_t_ptr, state_t1_ptr, lam_in_ptr, lam_out_ptr, gr
                                            ctypes.c_void_p(grad_force_ptr)))
 
 
-def lbf_step_static(params, src_ptr, dst_ptr, mask_ptr=None, sums_ptr=None):
+def lbf_step_static(params, src_ptr, dst_ptr, mask_ptr=None, sums_ptr=None, flags_ptr=None):
     """One step from src to dst with no device allocation (static scratch in the library)."""
     _check(load_library().lbf_step_static(ctypes.byref(params), ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr),
-                                          ctypes.c_void_p(mask_ptr), ctypes.c_void_p(sums_ptr)))
+                                          ctypes.c_void_p(mask_ptr), ctypes.c_void_p(sums_ptr),
+                                          ctypes.c_void_p(flags_ptr)))
 
 
 def lbf_destroy(ctx):

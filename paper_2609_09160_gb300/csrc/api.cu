@@ -181,6 +181,7 @@ struct lbf_ctx {
   int zchunk;
   dim3 fgrid, agrid;
   KernelInfo fwd, adj;
+  KernelInfo fwd_direct;  // the same step loading every site directly (sources TMA cannot read)
   bool tma;             // the forward kernel stages plane patches with TMA
   CUtensorMap tmap[2];  // tensor maps of the two state buffers (TMA source)
   bool sums_valid;
@@ -446,18 +447,21 @@ lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
   ++c->steps_done;
   CUtensorMap tm;
   std::memset(&tm, 0, sizeof(tm));
+  const KernelInfo* k = &c->fwd;
   if (c->tma) {
     if (src == c->state[0]) {
       tm = c->tmap[0];
     } else if (src == c->state[1]) {
       tm = c->tmap[1];
+    } else if (reinterpret_cast<uintptr_t>(src) % 16 != 0) {
+      k = &c->fwd_direct;  // a tensor map needs a 16-byte aligned base
     } else {
       lbf_status st = encode_state_map(c, src, &tm);
       if (st != LBF_OK) return st;
     }
   }
   void* args[] = {&a, &tm};
-  LBF_CUDA(cudaLaunchKernel(c->fwd.fn, c->fgrid, dim3(32, c->fwd.by + 2, 1), args, c->fwd.smem, c->stream));
+  LBF_CUDA(cudaLaunchKernel(k->fn, c->fgrid, dim3(32, k->by + 2, 1), args, k->smem, c->stream));
   return LBF_OK;
 }
 
@@ -615,8 +619,11 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
     delete c;
     return fail(LBF_ENOTSUP, "no population kernel for this combination");
   }
+  c->fwd_direct = c->tma ? forward_for(c->Q, c->storage, c->has_mask, c->two, params->force_field != nullptr, false,
+                                        params->rounding == LBF_ROUND_NEAREST)
+                         : c->fwd;
   c->adj = adjoint_for(c->Q, c->storage, c->has_mask);
-  if (c->fwd.fn == nullptr) {
+  if (c->fwd.fn == nullptr || c->fwd_direct.fn == nullptr) {
     delete c;
     return fail(LBF_ENOTSUP, "no kernel for this combination");
   }
@@ -625,6 +632,7 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
     return s;
   };
   if ((st = prepare(c->fwd)) != LBF_OK) return cleanup(st);
+  if ((st = prepare(c->fwd_direct)) != LBF_OK) return cleanup(st);
   if ((st = prepare(c->adj)) != LBF_OK) return cleanup(st);
 
   // z-chunk: the CTAs of one (x, y) tile column march through nz / chunks planes each. Choose the

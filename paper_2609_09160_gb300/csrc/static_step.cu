@@ -11,7 +11,9 @@
 // The array (kStaticScratchBytes) lives on every GPU that loads the library until the process
 // exits. All calls share it: two calls that overlap on the GPU (different streams, or host
 // threads) race on it; calls on one stream are ordered and safe. The counter and flags it holds
-// are cleared at the start of every call with cudaMemsetAsync.
+// are cleared at the start of every call with cudaMemsetAsync; after the step the flags word is
+// copied to the caller's flags_device (when given) with a device-to-device cudaMemcpyAsync, so a
+// caller without a context still learns whether the step was abandoned or went unstable.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -89,7 +91,7 @@ PFN_cuTensorMapEncodeTiled_v12000 static_encoder() {
 void lbf_internal_set_last_error(const char* msg);
 
 extern "C" lbf_status lbf_step_static(const lbf_params* params, const void* src, void* dst,
-                                      const uint8_t* mask_device, double* sums_device) {
+                                      const uint8_t* mask_device, double* sums_device, unsigned* flags_device) {
   auto fail = [](lbf_status s, const std::string& m) {
     lbf_internal_set_last_error(m.c_str());
     return s;
@@ -106,7 +108,10 @@ extern "C" lbf_status lbf_step_static(const lbf_params* params, const void* src,
   const long long N = (long long)nx * ny * nz;
   const size_t es = params->storage == LBF_F64 ? 8 : 4;
   PFN_cuTensorMapEncodeTiled_v12000 enc = static_encoder();
-  const bool tma = enc != nullptr && (size_t(nx) * es) % 16 == 0 && std::getenv("LBF_NO_TMA") == nullptr;
+  // TMA needs 16-byte row strides and a 16-byte aligned base; other buffers (e.g. a view into a
+  // larger tensor) take the kernel that loads every site directly
+  const bool tma = enc != nullptr && (size_t(nx) * es) % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
+                   std::getenv("LBF_NO_TMA") == nullptr;
   const KernelInfo k = forward_kernel_for(params->lattice, params->storage, mask_device != nullptr, false,
                                           params->force_field != nullptr, tma, false);
   if (k.fn == nullptr) return fail(LBF_ENOTSUP, "no kernel for this combination");
@@ -115,7 +120,8 @@ extern "C" lbf_status lbf_step_static(const lbf_params* params, const void* src,
   const long long tiles = (long long)((nx + 29) / 30) * ((ny + k.by - 1) / k.by);
   if (tiles > kStaticMaxBlocks)
     return fail(LBF_EINVAL, "lattice too wide for lbf_step_static: ceil(nx/30)*ceil(ny/" + std::to_string(k.by) +
-                                ") = " + std::to_string(tiles) + " exceeds " + std::to_string(kStaticMaxBlocks));
+                                ") = " + std::to_string(tiles) + " exceeds " + std::to_string(kStaticMaxBlocks) +
+                                " (" + std::to_string(k.by) + " = output rows per CTA of this kernel)");
   int zc = std::min(nz, 32);
   const long long max_chunks = kStaticMaxBlocks / tiles;
   if ((nz + zc - 1) / zc > max_chunks) zc = int((nz + max_chunks - 1) / max_chunks);
@@ -169,5 +175,8 @@ extern "C" lbf_status lbf_step_static(const lbf_params* params, const void* src,
   void* args[] = {&a, &tm};
   if ((e = cudaLaunchKernel(k.fn, grid, dim3(32, k.by + 2, 1), args, k.smem, stream)) != cudaSuccess)
     return fail(LBF_ECUDA, std::string("cudaLaunchKernel: ") + cudaGetErrorString(e));
+  if (flags_device != nullptr &&
+      (e = cudaMemcpyAsync(flags_device, flags, sizeof(unsigned), cudaMemcpyDeviceToDevice, stream)) != cudaSuccess)
+    return fail(LBF_ECUDA, std::string("cudaMemcpyAsync (flags): ") + cudaGetErrorString(e));
   return LBF_OK;
 }

@@ -25,6 +25,20 @@ def declared_symbols():
     return sorted(set(re.findall(r"\b(lbf_[a-z_0-9]+)\s*\(", text)))
 
 
+def test_every_declaration_cites_the_paper_or_says_it_has_no_counterpart():
+    """Each function of include/lbf.h carries, in the comment right above it, the passage of the
+    paper it implements ("Paper: Eq. ..., Sec. ...") or states that the paper has no counterpart."""
+    text = open(os.path.join(ROOT, "include", "lbf.h")).read()
+    body = text[text.index("} lbf_params;"):]
+    for name in declared_symbols():
+        m = re.search(r"/\*((?:(?!\*/).)*)\*/\s*[A-Za-z_][A-Za-z_0-9 *]*\b" + name + r"\s*\(", body, flags=re.S)
+        assert m is not None, f"{name}: no comment right above the declaration"
+        note = m.group(1)
+        assert "Paper:" in note, name
+        cited = re.search(r"Paper:.*(Eq\.|Sec\.|no counterpart)", note, flags=re.S)
+        assert cited is not None, f"{name}: the comment names no passage"
+
+
 def test_header_and_binding_agree():
     assert declared_symbols() == sorted(_lbf.EXPORTS)
 
