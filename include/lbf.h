@@ -156,7 +156,8 @@ lbf_status lbf_moments(lbf_ctx* ctx, void* dst, int dst_dtype, void* phi_dst);
 lbf_status lbf_reduce(lbf_ctx* ctx, double* out);
 
 /* Waits for the stream; LBF_EUNSTABLE as for lbf_reduce; LBF_EINTERNAL if a step was abandoned
-   (a bounded TMA wait gave up, or an index check of the LBF_DEBUG build failed).
+   (a bounded TMA wait gave up, or an index check of the LBF_DEBUG build failed). Such an error is
+   reported once and then cleared, so the context stays usable; the state it left is incomplete.
    Paper: no counterpart (stream completion and the library's instability check). */
 lbf_status lbf_synchronize(lbf_ctx* ctx);
 

@@ -154,6 +154,18 @@ def lbf_step_static(params, src_ptr, dst_ptr, mask_ptr=None, sums_ptr=None, flag
                                           ctypes.c_void_p(flags_ptr)))
 
 
+def lbf_debug_wait_probe(ctx, polls):
+    """Test hook of the LBF_DEBUG library (include/lbf_debug.h): a bounded mbarrier wait that gives
+    up after `polls` polls and sets the context's error flag. Raises if the loaded library is the
+    release build, which does not export it."""
+    lib = load_library()
+    if not hasattr(lib, "lbf_debug_wait_probe"):
+        raise RuntimeError("lbf_debug_wait_probe is exported by the LBF_DEBUG build (liblbf_debug.so) only")
+    fn = lib.lbf_debug_wait_probe
+    fn.restype, fn.argtypes = ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint]
+    _check(fn(ctx, polls))
+
+
 def lbf_destroy(ctx):
     _check(load_library().lbf_destroy(ctx))
 

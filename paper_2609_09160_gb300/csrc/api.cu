@@ -13,6 +13,9 @@
 #include <vector>
 
 #include "../../include/lbf.h"
+#ifdef LBF_DEBUG
+#include "../../include/lbf_debug.h"
+#endif
 #include "aux_kernels.cuh"
 #include "dispatch.cuh"
 
@@ -525,6 +528,20 @@ void host_absmax(const T* src, long long N, double m[3]) {
   }
 }
 
+#ifdef LBF_DEBUG
+// one CTA waits, with the fused step's bounded wait, on an mbarrier that nothing arrives on (no
+// copy is ever issued), and reports the give-up through the fused step's error bit
+__global__ void k_wait_probe(unsigned* flags, uint32_t polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u, polls)) atomicOr(flags, 2u);
+}
+#endif
+
 }  // namespace
 
 // lets the other translation units of the library report through lbf_last_error()
@@ -860,11 +877,26 @@ lbf_status lbf_moments(lbf_ctx* c, void* dst, int dt, void* phi_dst) {
   return LBF_OK;
 }
 
+#ifdef LBF_DEBUG
+lbf_status lbf_debug_wait_probe(lbf_ctx* c, unsigned polls) {
+  if (c == nullptr || polls < 1 || polls > kWaitPolls) return fail(LBF_EINVAL, "bad argument");
+  k_wait_probe<<<1, 32, 0, c->stream>>>(c->flags, polls);
+  LBF_CUDA(cudaGetLastError());
+  return LBF_OK;
+}
+#endif
+
 lbf_status lbf_synchronize(lbf_ctx* c) {
   if (c == nullptr) return fail(LBF_EINVAL, "NULL context");
   unsigned f = 0;
   LBF_CUDA(cudaMemcpyAsync(&f, c->flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
   LBF_CUDA(cudaStreamSynchronize(c->stream));
+  // the error bits are reported once: clear them so that the context stays usable
+  if (f & 14u) {
+    const unsigned keep = f & 1u;
+    LBF_CUDA(cudaMemcpyAsync(c->flags, &keep, sizeof(keep), cudaMemcpyHostToDevice, c->stream));
+    LBF_CUDA(cudaStreamSynchronize(c->stream));
+  }
   if (f & 8u) return fail(LBF_EINTERNAL, "an index check of the LBF_DEBUG build failed");
   if (f & 6u) return fail(LBF_EINTERNAL, (f & 4u) ? "a TMA stage was misaligned; the step was abandoned"
                                                   : "a TMA plane load did not complete in time; the step was abandoned");

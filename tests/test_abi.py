@@ -39,6 +39,16 @@ def test_every_declaration_cites_the_paper_or_says_it_has_no_counterpart():
         assert cited is not None, f"{name}: the comment names no passage"
 
 
+def test_debug_library_exports_its_test_hooks():
+    """liblbf_debug.so (LBF_DEBUG) exports every symbol of include/lbf_debug.h and of lbf.h."""
+    dbg = ctypes.CDLL(build.build(debug=True))
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "lbf_debug.h")).read(), flags=re.S)
+    hooks = sorted(set(re.findall(r"\b(lbf_[a-z_0-9]+)\s*\(", text)))
+    assert hooks == ["lbf_debug_wait_probe"]
+    for name in hooks + declared_symbols():
+        assert ctypes.cast(getattr(dbg, name), ctypes.c_void_p).value, name
+
+
 def test_header_and_binding_agree():
     assert declared_symbols() == sorted(_lbf.EXPORTS)
 
