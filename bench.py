@@ -279,29 +279,81 @@ def e2e_measure(torch, device, steps):
             "d2h_bytes_per_step": 48 + nbytes / steps}
 
 
-def cpu_baseline_oracle(target_seconds=12.0, shape=(4, 256, 256), max_steps=50):
-    """The FP64 oracle as it stands on the host cores, on a z-slab of the channel workload."""
+def _time_oracle_steps(step, target_seconds, max_steps):
+    """Run step() until target_seconds have passed (at least 2, at most max_steps calls)."""
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps and (steps < 2 or time.perf_counter() - t0 < target_seconds):
+        step()
+        steps += 1
+    return steps, time.perf_counter() - t0
+
+
+def cpu_baseline_oracle(target_seconds=10.0):
+    """The FP64 oracle as it stands, timed on the host cores: the headline sample (a 256x256x4
+    z-slab of the channel) on all cores and on one core, a 128x128x4 slab of the D3Q27 512^3
+    Taylor-Green workload, and the config-5 rollout (forward and its autograd adjoint) on a
+    128x64x4 slab of the adjoint channel. Each leg runs for about target_seconds."""
     import torch
 
     import oracle
     import synth
 
-    M0, solid = synth.channel(shape, 1e-3, seed=1)
-    t0 = time.perf_counter()
-    steps = 0
-    lat = oracle.D3Q19
-    F = oracle.lbm.as_field((1e-6, 0.0, 0.0), shape)
-    rho = oracle.lbm.as_scalar_field(1.0, shape)
-    om = oracle.lbm.as_scalar_field(oracle.lbm.omega_from_tau(0.9), shape)
-    f = oracle.lbm.populations_from_moments(lat, M0, F, rho)
-    while steps < max_steps and (steps < 2 or time.perf_counter() - t0 < target_seconds):
-        f = oracle.lbm.step(lat, f, F, rho, om, solid)
-        steps += 1
-    t = time.perf_counter() - t0
-    n = shape[0] * shape[1] * shape[2]
-    return {"value": n * steps / t / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"{steps} population-form FP64 steps on a {shape[2]}x{shape[1]}x{shape[0]} (x,y,z) slab of the "
-                      "channel (walls y=0,255, periodic z)"}
+    all_cores = torch.get_num_threads()
+
+    def channel_leg(threads, seconds, max_steps):
+        shape = (4, 256, 256)
+        M0, solid = synth.channel(shape, 1e-3, seed=1)
+        F = oracle.lbm.as_field((1e-6, 0.0, 0.0), shape)
+        rho = oracle.lbm.as_scalar_field(1.0, shape)
+        om = oracle.lbm.as_scalar_field(oracle.lbm.omega_from_tau(0.9), shape)
+        st = {"f": oracle.lbm.populations_from_moments(oracle.D3Q19, M0, F, rho)}
+        torch.set_num_threads(threads)
+        try:
+            steps, t = _time_oracle_steps(lambda: st.update(f=oracle.lbm.step(oracle.D3Q19, st["f"], F, rho, om, solid)),
+                                          seconds, max_steps)
+        finally:
+            torch.set_num_threads(all_cores)
+        return {"value": round(256 * 256 * 4 * steps / t / 1e6, 4), "unit": "MLUPS", "cores": threads,
+                "sample": f"{steps} population-form FP64 D3Q19 steps on a 256x256x4 (x,y,z) slab of the channel"}
+
+    def d3q27_leg(seconds):
+        shape = (4, 128, 128)
+        M = synth.taylor_green_perturbed(128, 0.04, 0.55, 0.01, seed=3)[:, :4].contiguous()
+        F = oracle.lbm.as_field((0.0, 0.0, 0.0), shape)
+        rho = oracle.lbm.as_scalar_field(1.0, shape)
+        om = oracle.lbm.as_scalar_field(oracle.lbm.omega_from_tau(0.55), shape)
+        st = {"f": oracle.lbm.populations_from_moments(oracle.D3Q27, M, F, rho)}
+        steps, t = _time_oracle_steps(lambda: st.update(f=oracle.lbm.step(oracle.D3Q27, st["f"], F, rho, om, None)),
+                                      seconds, 200)
+        return {"value": round(128 * 128 * 4 * steps / t / 1e6, 4), "unit": "MLUPS", "cores": all_cores,
+                "sample": f"{steps} population-form FP64 D3Q27 steps on a 128x128x4 slab of the 128^3 "
+                          "Taylor-Green + perturbation workload"}
+
+    def adjoint_leg(steps=8):
+        shape = (4, 64, 128)
+        mask = synth.channel_walls(shape)
+        F = synth.random_field(shape, 1e-6, seed=70, mask=mask)
+        u_tgt = synth.random_field(shape, 1e-4, seed=71)
+        M0 = torch.zeros((10,) + shape, dtype=torch.float64)
+        t0 = time.perf_counter()
+        oracle.adjoint.rollout_loss(oracle.D3Q19, M0, F, steps, 0.9, u_tgt, mask)
+        t1 = time.perf_counter()
+        oracle.adjoint.rollout_gradient(oracle.D3Q19, M0, F, steps, 0.9, u_tgt, mask)
+        t2 = time.perf_counter()
+        fwd, both = t1 - t0, t2 - t1
+        n = 128 * 64 * 4
+        return {"forward_MLUPS": round(n * steps / fwd / 1e6, 4), "adjoint_over_forward": round((both - fwd) / fwd, 3),
+                "cores": all_cores,
+                "sample": f"config-5 rollout of {steps} steps on a 128x64x4 (x,y,z) slab of the adjoint channel: "
+                          "oracle forward, then forward + autograd backward"}
+
+    head = channel_leg(all_cores, target_seconds, 50)
+    legs = {"channel256_slab_1core": channel_leg(1, target_seconds / 2, 10),
+            "tg128_d3q27_slab": d3q27_leg(target_seconds / 2),
+            "adjoint_config5_slab": adjoint_leg()}
+    return {"value": head["value"], "unit": "MLUPS", "cores": all_cores, "kind": "oracle", "sample": head["sample"],
+            "cores_listed": [all_cores, 1], "legs": legs}
 
 
 def extras(torch, device, quick):
@@ -366,12 +418,59 @@ def extras(torch, device, quick):
     return out
 
 
-def energy_per_update(clocks, seconds_per_step, sites):
-    """nJ per lattice update from the median board power sampled during the timed steps."""
-    if not clocks or clocks.get("power_w") is None:
-        return None
-    return {"nJ_per_lup": round(clocks["power_w"] * seconds_per_step / sites * 1e9, 4), "power_w": clocks["power_w"],
-            "source": "nvidia-smi power.draw, median over the timed region"}
+class NvmlEnergy:
+    """Board energy counter of one GPU through NVML (nvmlDeviceGetTotalEnergyConsumption, mJ since
+    the driver loaded): the quantity the paper integrates for its energy per lattice update. A
+    read-only query; None where NVML is not available."""
+
+    def __init__(self, uuid):
+        import ctypes
+
+        self.lib = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(uuid.encode()), ctypes.byref(h)) != 0:
+                return
+            self.lib, self.handle, self.ct = lib, h, ctypes
+        except Exception:
+            self.lib = None
+
+    def read_mj(self):
+        if self.lib is None:
+            return None
+        v = self.ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.handle, self.ct.byref(v)) != 0:
+            return None
+        return int(v.value)
+
+
+def energy_leg(torch, s, gpu_id, seconds_per_step, target_seconds=2.5):
+    """Energy per lattice update (the paper's metric, Sec. 5): the NVML energy counter read before
+    and after at least ~2.5 s of steps, divided by the lattice updates; board power sampled by
+    nvidia-smi over the same steps. Returns None without NVML."""
+    meter = NvmlEnergy(gpu_id)
+    if meter.lib is None:
+        return {"nJ_per_lup": None, "source": "NVML not available"}
+    steps = max(200, int(target_seconds / max(seconds_per_step, 1e-6)))
+    s.step(10)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id) as clk:
+        e0 = meter.read_mj()
+        t0 = time.perf_counter()
+        s.step(steps)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e1 = meter.read_mj()
+    clocks = clk.summary()
+    if e0 is None or e1 is None or e1 <= e0:
+        return {"nJ_per_lup": None, "source": "NVML energy counter did not advance"}
+    joules = (e1 - e0) / 1e3
+    return {"nJ_per_lup": round(joules / (s.N * steps) * 1e9, 4), "power_w": round(joules / (t1 - t0), 1),
+            "seconds": round(t1 - t0, 3), "steps": steps, "clocks_during": clocks,
+            "source": "NVML nvmlDeviceGetTotalEnergyConsumption, difference over the steps of this leg"}
 
 
 def max_over_ranks(torch, dist, t, device):
@@ -455,11 +554,12 @@ def run_ours(args):
                      "bytes_per_lup": bpl, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
         "gpu_launches": args.steps,
         "clocks": clocks,
-        # board power (median of the samples in the timed region) x time per step / sites: the
-        # energy per lattice update the paper reports for its weak-scaling runs
-        "energy": energy_per_update(clocks, t / args.steps, n),
         "sums_after": {"sum_p": sums[0], "sum_ux": sums[1]},
     }
+    if world == 1 and not args.kernel_only:
+        # energy per lattice update: NVML energy counter over a separate leg of >= 2.5 s of steps
+        # (the timed region above can be far shorter than the power sampling interval)
+        line["energy"] = energy_leg(torch, s, gpu_identifier(torch, device), t / args.steps)
     if world == 1 and not args.kernel_only and args.workload == "channel256":
         line["e2e"] = e2e_measure(torch, device, args.steps)
         line["cpu_baseline"] = cpu_baseline_oracle()

@@ -1,6 +1,6 @@
 """GPU parity of the adjoint kernel and of the checkpointed Rollout with the oracle's FP64
 gradients, and the config-5 finite-difference check (128x64x64 channel, per-site force,
-500 steps, checkpoints every 50) in FP64 on the GPU."""
+500 steps, checkpoints every 50) of the FP64 and of the FP32 rollout gradient."""
 import numpy as np
 import pytest
 import torch
@@ -71,28 +71,23 @@ def test_rollout_gradient_matches_oracle(lattice, storage):
     assert max(errs.values()) < tol, errs
 
 
-def test_config5_adjoint_matches_central_differences():
-    """128(x) x 64(y) x 64(z) channel, walls at y = 0 and 63, per-site force N(0, 1e-12) on the
-    fluid, loss = mean |u(500) - u_target|^2 over the fluid, checkpoints every 50 steps. FP64 GPU
-    forward for the differences (eps = 1e-7 on one force component; eps 1e-6 gives the same
-    values: the loss is a near-quadratic function of F), 16 sites x 3 components, agreement 1e-4."""
-    shape = (64, 64, 128)
-    steps, K, tau = 500, 50, 0.9
+CONFIG5 = dict(shape=(64, 64, 128), steps=500, K=50, tau=0.9)
+
+
+@pytest.fixture(scope="module")
+def config5_central_differences():
+    """Config 5: 128(x) x 64(y) x 64(z) channel, walls at y = 0 and 63, per-site force N(0, 1e-12)
+    on the fluid, loss = mean |u(500) - u_target|^2 over the fluid. Central differences of the loss
+    by the FP64 GPU forward (eps = 1e-7 on one force component; eps = 1e-6 must give the same value:
+    the loss is a near-quadratic function of F) at 16 seeded fluid sites x 3 components.
+    Returns (picks, fd[16, 3], plateau[16, 3], inputs)."""
+    shape, steps, tau = CONFIG5["shape"], CONFIG5["steps"], CONFIG5["tau"]
     mask = synth.channel_walls(shape)
     F64 = synth.random_field(shape, 1e-6, seed=70, mask=mask).cuda().contiguous()
     u_tgt = synth.random_field(shape, 1e-4, seed=71).cuda()
     M0 = torch.zeros((10,) + shape, dtype=torch.float64, device="cuda")
     fluid = (~mask).cuda().double()
     nfl = fluid.sum()
-
-    Fd = F64.clone().requires_grad_(True)
-    s = Solver(shape, lattice=19, tau=tau, storage="f64", force_field=Fd, mask=mask)
-    MT = rollout(Fd, M0, s, steps, K)
-    d = (MT[1:4] - u_tgt) * fluid
-    L = (d * d).sum() / nfl
-    L.backward()
-    g = s.grad_force64
-
     F_fd = F64.clone()
     s_fd = Solver(shape, lattice=19, tau=tau, storage="f64", force_field=F_fd, mask=mask)
 
@@ -106,8 +101,9 @@ def test_config5_adjoint_matches_central_differences():
     rng = np.random.default_rng(72)
     fl = torch.nonzero(~mask).numpy()
     picks = fl[rng.choice(len(fl), 16, replace=False)]
-    gmax = g.abs().max().item()
-    for z, y, x in picks:
+    fd = np.zeros((16, 3))
+    plateau = np.zeros((16, 3))
+    for k, (z, y, x) in enumerate(picks):
         for a in range(3):
             vals = []
             for eps in (1e-7, 1e-6):
@@ -117,7 +113,49 @@ def test_config5_adjoint_matches_central_differences():
                 F_fd[a, z, y, x] -= 2 * eps
                 lm = loss()
                 vals.append((lp - lm) / (2 * eps))
-            fd = vals[0]
-            assert abs(vals[0] - vals[1]) < 1e-4 * max(abs(fd), 1e-3 * gmax)  # plateau
-            got = g[a, z, y, x].item()
-            assert abs(got - fd) < 1e-4 * max(abs(fd), 1e-3 * gmax), (a, z, y, x, got, fd)
+            fd[k, a] = vals[0]
+            plateau[k, a] = abs(vals[0] - vals[1])
+    return picks, fd, plateau, dict(mask=mask, F64=F64, u_tgt=u_tgt, fluid=fluid, nfl=nfl)
+
+
+def config5_adjoint(storage, inp):
+    """dL/dF of config 5 by the checkpointed rollout: forward in the storage precision, the
+    adjoint state in the compute precision, the force gradient accumulated in FP64."""
+    shape, steps, K, tau = CONFIG5["shape"], CONFIG5["steps"], CONFIG5["K"], CONFIG5["tau"]
+    cdt = CDT[storage]
+    Fd = inp["F64"].to(cdt).clone().requires_grad_(True)
+    s = Solver(shape, lattice=19, tau=tau, storage=storage, force_field=Fd, mask=inp["mask"])
+    M0 = torch.zeros((10,) + shape, dtype=cdt, device="cuda")
+    MT = rollout(Fd, M0, s, steps, K)
+    fluid = inp["fluid"].to(cdt)
+    d = (MT[1:4] - inp["u_tgt"].to(cdt)) * fluid
+    L = (d * d).sum() / fluid.sum()
+    L.backward()
+    return s.grad_force64
+
+
+def _compare(g, picks, fd, plateau):
+    gmax = g.abs().max().item()
+    worst = 0.0
+    for k, (z, y, x) in enumerate(picks):
+        for a in range(3):
+            scale = max(abs(fd[k, a]), 1e-3 * gmax)
+            assert plateau[k, a] < 1e-4 * scale
+            worst = max(worst, abs(g[a, z, y, x].item() - fd[k, a]) / scale)
+    return worst
+
+
+def test_config5_adjoint_matches_central_differences(config5_central_differences):
+    """The FP64 rollout gradient agrees with the central differences to 1e-4."""
+    picks, fd, plateau, inp = config5_central_differences
+    worst = _compare(config5_adjoint("f64", inp), picks, fd, plateau)
+    assert worst < 1e-4, worst
+
+
+def test_config5_fp32_adjoint_matches_central_differences(config5_central_differences):
+    """The configuration the bench times: FP32 forward and adjoint state with FP64 accumulation of
+    the force gradient, against the same FP64 central differences, to 1e-4 (the spec bar)."""
+    picks, fd, plateau, inp = config5_central_differences
+    worst = _compare(config5_adjoint("f32", inp), picks, fd, plateau)
+    print(f"config-5 FP32 adjoint: worst relative difference to FP64 central differences {worst:.3e}")
+    assert worst < 1e-4, worst
