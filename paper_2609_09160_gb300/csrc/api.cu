@@ -102,13 +102,19 @@ lbf_status check_params(const lbf_params* p) {
   return LBF_OK;
 }
 
-int grid_x(int nx) { return (nx + FwdTile<8>::XOUT - 1) / FwdTile<8>::XOUT; }
+int grid_x(int nx, int xout = FwdTile<8>::XOUT) { return (nx + xout - 1) / xout; }
 int grid_y(int ny, int by) { return (ny + by - 1) / by; }
 int fwd_by(int lattice, int storage, bool mask, bool two) {
   return fwd_rows_lattice(lattice == LBF_D3Q19 ? 19 : 27, int(storage_bytes(storage)), mask, two,
                           lattice == LBF_D3Q27H);
 }
 int min_zchunk(int nz) { return std::min(8, nz); }
+// output rows of the line-aligned kernel for these parameters (0 when it is not built for them)
+int aligned_by(const lbf_params* p) {
+  if (p->two_component || p->populations || p->storage == LBF_F64) return 0;
+  return al_rows(p->lattice == LBF_D3Q19 ? 19 : 27, int(storage_bytes(p->storage)), p->mask != nullptr,
+                 p->lattice == LBF_D3Q27H);
+}
 
 bool make_layout(const lbf_params* p, Layout* L) {
   if (check_params(p) != LBF_OK) return false;
@@ -137,7 +143,10 @@ bool make_layout(const lbf_params* p, Layout* L) {
     L->phi[0] = L->phi[1] = L->F[0] = L->F[1] = L->G = 0;
   }
   const long long gz = (p->nz + min_zchunk(p->nz) - 1) / min_zchunk(p->nz);
-  L->npartials = std::max<long long>((long long)grid_x(p->nx) * grid_y(p->ny, fwd_by(p->lattice, p->storage, p->mask != nullptr, p->two_component != 0)) * gz, 1024);
+  // per-block partial sums of the largest grid either forward kernel can launch
+  long long tiles = (long long)grid_x(p->nx) * grid_y(p->ny, fwd_by(p->lattice, p->storage, p->mask != nullptr, p->two_component != 0));
+  if (const int aby = aligned_by(p)) tiles = std::max(tiles, (long long)grid_x(p->nx, 32) * grid_y(p->ny, aby));
+  L->npartials = std::max<long long>(tiles * gz, 1024);
   L->partials = take(size_t(L->npartials) * 8 * sizeof(double));
   L->scal = take(64 * sizeof(double));
   L->staging_bytes = std::min<size_t>(kStagingMax, size_t(11) * 8 * size_t(N));
@@ -185,8 +194,11 @@ struct lbf_ctx {
   dim3 fgrid, agrid;
   KernelInfo fwd, adj;
   KernelInfo fwd_direct;  // the same step loading every site directly (sources TMA cannot read)
+  KernelInfo fwd_tma30;   // the 30-column TMA kernel (buffers the aligned kernel cannot address)
   bool tma;             // the forward kernel stages plane patches with TMA
+  bool aligned;         // the forward kernel is the line-aligned one (TMA loads and stores)
   CUtensorMap tmap[2];  // tensor maps of the two state buffers (TMA source)
+  CUtensorMap smap[2];  // tensor maps of the two state buffers (TMA store destination)
   bool sums_valid;
   bool unstable_seen;
   double omega, nu_l, nu_h;
@@ -226,8 +238,8 @@ bool tma_eligible(int storage, int nx) {
          std::getenv("LBF_NO_TMA") == nullptr;
 }
 
-// 4-D map over a state buffer: dims (x, y, z, field), box (box_x, rows, 1, 10)
-lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out);
+// 4-D map over a state buffer: dims (x, y, z, field), box (box_x, box_y, 1, 10)
+lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out, int box_x, int box_y);
 KernelInfo adjoint_for(int Q, int storage, bool mask) { return adjoint_kernel_for(Q, storage, mask); }
 
 lbf_status prepare(const KernelInfo& k) {
@@ -419,7 +431,7 @@ lbf_status pop_moments(lbf_ctx* c) {
   return LBF_OK;
 }
 
-lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out) {
+lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out, int box_x, int box_y) {
   CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   switch (c->storage) {
     case LBF_F64: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
@@ -430,7 +442,7 @@ lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out
   const cuuint64_t es = storage_bytes(c->storage);
   const cuuint64_t dims[4] = {cuuint64_t(c->nx), cuuint64_t(c->ny), cuuint64_t(c->nz), 10};
   const cuuint64_t strides[3] = {es * c->nx, es * c->nx * c->ny, es * cuuint64_t(c->N)};
-  const cuuint32_t box[4] = {cuuint32_t(c->fwd.box_x), cuuint32_t(c->fwd.by + 2), 1, 10};
+  const cuuint32_t box[4] = {cuuint32_t(box_x), cuuint32_t(box_y), 1, 10};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = tensor_map_encoder()(out, dt, 4, const_cast<void*>(base), dims, strides, box, estr,
                                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -448,23 +460,43 @@ lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
   }
   FwdParams a = forward_params(c, src, dst, reduce);
   ++c->steps_done;
-  CUtensorMap tm;
+  CUtensorMap tm, sm;
   std::memset(&tm, 0, sizeof(tm));
+  std::memset(&sm, 0, sizeof(sm));
   const KernelInfo* k = &c->fwd;
-  if (c->tma) {
+  const bool aligned16 = reinterpret_cast<uintptr_t>(src) % 16 == 0;  // a tensor map needs a 16-byte base
+  if (c->aligned) {
+    const int ks = src == c->state[0] ? 0 : (src == c->state[1] ? 1 : -1);
+    const int kd = dst == c->state[0] ? 0 : (dst == c->state[1] ? 1 : -1);
+    if (ks >= 0 && kd >= 0) {
+      tm = c->tmap[ks];
+      sm = c->smap[kd];
+    } else if (aligned16 && reinterpret_cast<uintptr_t>(dst) % 16 == 0) {
+      lbf_status st = encode_state_map(c, src, &tm, c->fwd.box_x, c->fwd.by + 2);
+      if (st == LBF_OK) st = encode_state_map(c, dst, &sm, 32, c->fwd.by);
+      if (st != LBF_OK) return st;
+    } else if (aligned16) {  // dst cannot take TMA stores: 30-column kernel with TMA loads
+      k = &c->fwd_tma30;
+      lbf_status st = encode_state_map(c, src, &tm, k->box_x, k->by + 2);
+      if (st != LBF_OK) return st;
+    } else {
+      k = &c->fwd_direct;
+    }
+  } else if (c->tma) {
     if (src == c->state[0]) {
       tm = c->tmap[0];
     } else if (src == c->state[1]) {
       tm = c->tmap[1];
-    } else if (reinterpret_cast<uintptr_t>(src) % 16 != 0) {
-      k = &c->fwd_direct;  // a tensor map needs a 16-byte aligned base
+    } else if (!aligned16) {
+      k = &c->fwd_direct;
     } else {
-      lbf_status st = encode_state_map(c, src, &tm);
+      lbf_status st = encode_state_map(c, src, &tm, k->box_x, k->by + 2);
       if (st != LBF_OK) return st;
     }
   }
-  void* args[] = {&a, &tm};
-  LBF_CUDA(cudaLaunchKernel(k->fn, c->fgrid, dim3(32, k->by + 2, 1), args, k->smem, c->stream));
+  void* args[] = {&a, &tm, &sm};
+  const dim3 grid(grid_x(c->nx, k->xout), grid_y(c->ny, k->by), c->fgrid.z);
+  LBF_CUDA(cudaLaunchKernel(k->fn, grid, dim3(32, k->threads / 32, 1), args, k->smem, c->stream));
   return LBF_OK;
 }
 
@@ -628,8 +660,17 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   set_scales(c, m0);
 
   c->tma = tma_eligible(c->storage, c->nx);
-  c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two, params->force_field != nullptr, c->tma,
-                       params->rounding == LBF_ROUND_NEAREST);
+  const bool nearest = params->rounding == LBF_ROUND_NEAREST;
+  c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two, params->force_field != nullptr, c->tma, nearest);
+  c->fwd_tma30 = c->fwd;
+  c->aligned = false;
+  if (c->tma && !c->two && !c->pops && std::getenv("LBF_NO_ALIGNED") == nullptr) {
+    const KernelInfo al = aligned_kernel_for(c->Q, c->storage, c->has_mask, params->force_field != nullptr, nearest);
+    if (al.fn != nullptr) {
+      c->fwd = al;
+      c->aligned = true;
+    }
+  }
   c->popk = c->pops ? pop_kernels_for(c->Q, c->storage, c->has_mask, params->force_field != nullptr)
                     : PopKernels{nullptr, nullptr, nullptr};
   if (c->pops && c->popk.step == nullptr) {
@@ -649,6 +690,7 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
     return s;
   };
   if ((st = prepare(c->fwd)) != LBF_OK) return cleanup(st);
+  if ((st = prepare(c->fwd_tma30)) != LBF_OK) return cleanup(st);
   if ((st = prepare(c->fwd_direct)) != LBF_OK) return cleanup(st);
   if ((st = prepare(c->adj)) != LBF_OK) return cleanup(st);
 
@@ -660,7 +702,7 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c->fwd.fn, c->fwd.threads, c->fwd.smem) != cudaSuccess)
     return cleanup(fail(LBF_ECUDA, std::string("device query failed: ") + cudaGetErrorString(cudaGetLastError())));
   per_sm = std::max(per_sm, 1);
-  const long long tiles = (long long)grid_x(c->nx) * grid_y(c->ny, c->fwd.by);
+  const long long tiles = (long long)grid_x(c->nx, c->fwd.xout) * grid_y(c->ny, c->fwd.by);
   const double resident = double(sms) * per_sm;
   int zc = c->nz;
   double best = 1e30;
@@ -682,13 +724,19 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
     if (v >= 1) zc = std::max(min_zchunk(c->nz), v);
   }
   c->zchunk = std::min(zc, c->nz);
-  c->fgrid = dim3(grid_x(c->nx), grid_y(c->ny, c->fwd.by), (c->nz + c->zchunk - 1) / c->zchunk);
+  c->fgrid = dim3(grid_x(c->nx, c->fwd.xout), grid_y(c->ny, c->fwd.by), (c->nz + c->zchunk - 1) / c->zchunk);
   c->agrid = c->adj.fn ? dim3(grid_x(c->nx), grid_y(c->ny, c->adj.by), (c->nz + c->zchunk - 1) / c->zchunk) : dim3(1, 1, 1);
   if (c->tma) {
-    for (int k = 0; k < 2; ++k)
-      if ((st = encode_state_map(c, c->state[k], &c->tmap[k])) != LBF_OK) return cleanup(st);
+    for (int k = 0; k < 2; ++k) {
+      if ((st = encode_state_map(c, c->state[k], &c->tmap[k], c->fwd.box_x, c->fwd.by + 2)) != LBF_OK) return cleanup(st);
+      if (c->aligned && (st = encode_state_map(c, c->state[k], &c->smap[k], 32, c->fwd.by)) != LBF_OK) return cleanup(st);
+    }
   }
-  if (forward_blocks(c) > L.npartials) return cleanup(fail(LBF_EINTERNAL, "partials buffer too small"));
+  // every grid launch_forward can use must fit the partial sums
+  const long long gz = c->fgrid.z;
+  for (const KernelInfo* k : {&c->fwd, &c->fwd_tma30, &c->fwd_direct})
+    if ((long long)grid_x(c->nx, k->xout) * grid_y(c->ny, k->by) * gz > L.npartials)
+      return cleanup(fail(LBF_EINTERNAL, "partials buffer too small"));
 
   cudaStream_t s = c->stream;
   if (cudaMemsetAsync(c->state[0], 0, 10 * c->N * storage_bytes(c->storage), s) != cudaSuccess ||

@@ -6,6 +6,7 @@
 #include "adjoint.cuh"
 #include "population.cuh"
 #include "stream_collide.cuh"
+#include "stream_collide_aligned.cuh"
 
 namespace lbf {
 
@@ -21,6 +22,8 @@ struct KernelInfo {
   int threads;      // threads per CTA
   int by;           // output rows per CTA
   int box_x;        // TMA box width in elements (0: the kernel loads without TMA)
+  int xout = 30;    // output columns per CTA: 30 (k_stream_collide) or 32 (k_stream_collide_al)
+  bool store_map = false;  // the kernel also takes a tensor map of dst (TMA stores)
 };
 
 template <class L, class S, bool MASK, bool TWO, bool FF, bool TMA, bool RN>
@@ -70,6 +73,42 @@ KernelInfo forward_kernel_ls(bool mask, bool two, bool field, bool tma, bool nea
              : forward_kernel_s<L, S, false, false>(mask, two, field);
 }
 
+// line-aligned kernel with TMA stores (FP32 and 16-bit storage, single component)
+template <class L, class S, bool MASK, bool FF, bool RN>
+KernelInfo al_info() {
+  constexpr int TY = al_rows(L::Q, int(sizeof(S)), MASK, L::HIGH);
+  KernelInfo k;
+  k.fn = reinterpret_cast<const void*>(&k_stream_collide_al<L, S, TY, MASK, FF, RN>);
+  k.smem = al_smem_bytes<L, S, TY, MASK>();
+  k.threads = AlTile<S, TY>::THREADS;
+  k.by = TY;
+  k.box_x = AlTile<S, TY>::BX;
+  k.xout = 32;
+  k.store_map = true;
+  return k;
+}
+
+template <class L, class S, bool RN>
+KernelInfo aligned_kernel_s(bool mask, bool field) {
+  if (mask) return field ? al_info<L, S, true, true, RN>() : al_info<L, S, true, false, RN>();
+  return field ? al_info<L, S, false, true, RN>() : al_info<L, S, false, false, RN>();
+}
+
+template <class L, class S>
+KernelInfo aligned_kernel_ls(bool mask, bool field, bool nearest) {
+  if constexpr (std::is_same<S, double>::value) {
+    (void)mask;
+    (void)field;
+    (void)nearest;
+    return KernelInfo{nullptr, 0, 0, 0, 0};  // FP64 storage keeps the 30-column kernel
+  } else {
+    if constexpr (Codec<S>::scaled) {
+      if (nearest) return aligned_kernel_s<L, S, true>(mask, field);
+    }
+    return aligned_kernel_s<L, S, false>(mask, field);
+  }
+}
+
 // population-form reference kernels of lattice L, storage S (FP32/FP64 only; nulls otherwise)
 struct PopKernels {
   const void* step;     // k_pop_step
@@ -99,6 +138,7 @@ PopKernels pop_kernels_ls(bool mask, bool field) {
 // entry points implemented per (lattice, storage) translation unit
 #define LBF_DECLARE_TU(q, s)                                                             \
   KernelInfo forward_kernel_q##q##_s##s(bool mask, bool two, bool field, bool tma, bool nearest); \
+  KernelInfo aligned_kernel_q##q##_s##s(bool mask, bool field, bool nearest);                    \
   PopKernels pop_kernels_q##q##_s##s(bool mask, bool field);                                        \
   KernelInfo adjoint_kernel_q##q##_s##s(bool mask);
 LBF_DECLARE_TU(19, 0)
@@ -138,6 +178,26 @@ inline KernelInfo forward_kernel_for(int lattice, int storage, bool mask, bool t
     case ST_BF16:
       return q19 ? forward_kernel_q19_s3(mask, two, field, tma, nearest) : forward_kernel_q27_s3(mask, two, field, tma, nearest);
   }
+  return KernelInfo{nullptr, 0, 0, 0, 0};
+}
+
+// line-aligned kernel with TMA stores; fn == nullptr where it is not built (FP64 storage)
+inline KernelInfo aligned_kernel_for(int lattice, int storage, bool mask, bool field, bool nearest) {
+#define LBF_AL_CASE(q)                                                     \
+  switch (storage) {                                                      \
+    case ST_F64: return aligned_kernel_q##q##_s0(mask, field, nearest);   \
+    case ST_F32: return aligned_kernel_q##q##_s1(mask, field, nearest);   \
+    case ST_F16: return aligned_kernel_q##q##_s2(mask, field, nearest);   \
+    case ST_BF16: return aligned_kernel_q##q##_s3(mask, field, nearest);  \
+  }
+  if (lattice == 19) {
+    LBF_AL_CASE(19)
+  } else if (lattice == 27) {
+    LBF_AL_CASE(27)
+  } else if (lattice == 127) {
+    LBF_AL_CASE(127)
+  }
+#undef LBF_AL_CASE
   return KernelInfo{nullptr, 0, 0, 0, 0};
 }
 
