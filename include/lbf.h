@@ -10,8 +10,9 @@
  * D3Q27 with second-order truncation are supported, and D3Q27h: the D3Q27 velocities with the
  * complete Hermite basis, whose third- to sixth-order coefficients are rebuilt from the stored
  * moments by the recursive closure (Sec. 2; the state is the same 10 fields). The conservative
- * Allen-Cahn phase field of
- * Eq. (ACeq) with the capillary force provides the two-component coupling at equal densities.
+ * Allen-Cahn phase field of Eq. (ACeq) with the force split of Sec. 2 (capillary, body, pressure
+ * and viscous-gradient forces) provides the two-component coupling, with density and viscosity
+ * contrast.
  *
  * Conventions shared by every call
  *  - Sites are indexed (z, y, x) with x fastest; a field is nz*ny*nx contiguous values.
@@ -85,10 +86,14 @@ typedef struct {
                            be rewritten by the caller between steps; NULL = none. */
   const uint8_t* mask;  /* optional HOST pointer, nz*ny*nx bytes, nonzero = solid; copied by
                            lbf_create; NULL = all fluid. */
-  int two_component;    /* nonzero: conservative Allen-Cahn phase field coupled through the
-                           capillary force (Eq. ACeq, F^s = mu grad phi); requires mask == NULL
-                           and rho_l == rho_h (the pressure and viscous-gradient forces of the
-                           paper vanish there and are not built). */
+  int two_component;    /* nonzero: conservative Allen-Cahn phase field (Eq. ACeq) coupled through the
+                           force split of Sec. 2, F = F^s + F^b + F^p + F^nu: the capillary force
+                           F^s = mu grad phi, F^b = force + rho(phi) body_accel, and with
+                           rho_l != rho_h the pressure force F^p = -p* cs2 grad rho and the
+                           viscous-gradient force F^nu = -(nu omega / cs2) a*_neq . grad rho (a*
+                           the raw streamed moments). Walls (mask) keep phi frozen and u = 0 at
+                           solid sites (no wetting model). A density contrast or walls need
+                           LBF_F32 or LBF_F64 storage; force_field is not supported. */
   double rho_l, rho_h;  /* densities of the light (phi = 0) and heavy (phi = 1) phase */
   double tau_l, tau_h;  /* relaxation times; nu(phi) = nu_l + phi (nu_h - nu_l) */
   double sigma, width;  /* surface tension and interface width W: beta = 12 sigma/W,
@@ -107,6 +112,9 @@ typedef struct {
                            moments out); state buffers hold Q fields; the sums of lbf_reduce are
                            computed from the state when asked. FP32/FP64 storage, single
                            component, no adjoint (LBF_ENOTSUP). */
+  double body_accel[3]; /* two_component only: uniform body acceleration a; F^b gains rho(phi) a
+                           (the layered Poiseuille flow of Sec. 4 is driven this way). Must be 0
+                           for a single component (use force). */
 } lbf_params;
 
 /* Workspace bytes the context needs for these parameters, 0 if the parameters are invalid.

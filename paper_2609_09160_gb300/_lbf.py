@@ -28,7 +28,7 @@ class lbf_params(ctypes.Structure):
         ("rho_l", ctypes.c_double), ("rho_h", ctypes.c_double), ("tau_l", ctypes.c_double),
         ("tau_h", ctypes.c_double), ("sigma", ctypes.c_double), ("width", ctypes.c_double),
         ("diffusivity", ctypes.c_double), ("scale_hint", ctypes.c_double * 3), ("stream", ctypes.c_void_p),
-        ("rounding", ctypes.c_int), ("populations", ctypes.c_int),
+        ("rounding", ctypes.c_int), ("populations", ctypes.c_int), ("body_accel", ctypes.c_double * 3),
     ]
 
 

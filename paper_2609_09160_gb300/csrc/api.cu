@@ -61,7 +61,7 @@ size_t storage_bytes(int storage) {
 size_t compute_bytes(int storage) { return storage == LBF_F64 ? 8 : 4; }
 
 struct Layout {
-  size_t state[2], mom, mask, phi[2], F[2], G, partials, scal, staging, total;
+  size_t state[2], mom, mask, phi[2], F[2], G, gphi, partials, scal, staging, total;
   long long npartials;
   size_t staging_bytes;
 };
@@ -85,22 +85,29 @@ lbf_status check_params(const lbf_params* p) {
   if (p->populations && (p->ny > 65535 || p->nz > 65535))
     return fail(LBF_ENOTSUP, "the population representation launches one block row per (y, z): ny, nz <= 65535");
   for (int a = 0; a < 3; ++a)
-    if (!std::isfinite(p->force[a])) return fail(LBF_EINVAL, "force must be finite");
+    if (!std::isfinite(p->force[a]) || !std::isfinite(p->body_accel[a]))
+      return fail(LBF_EINVAL, "force and body_accel must be finite");
   if (p->two_component) {
     if (!(p->tau_l > 0.5) || !(p->tau_h > 0.5)) return fail(LBF_EINVAL, "tau_l and tau_h must be > 0.5");
     if (!(p->rho_l > 0.0) || !(p->rho_h > 0.0)) return fail(LBF_EINVAL, "rho_l and rho_h must be > 0");
-    if (p->rho_l != p->rho_h)
-      return fail(LBF_ENOTSUP,
-                  "two-component with a density contrast needs the pressure and viscous-gradient forces, which are not built");
-    if (p->mask != nullptr) return fail(LBF_ENOTSUP, "two-component with walls (no wetting condition) is not built");
+    const bool wide = p->storage == LBF_F64 || p->storage == LBF_F32;
+    if (p->rho_l != p->rho_h && !wide)
+      return fail(LBF_ENOTSUP, "two-component with a density contrast needs LBF_F32 or LBF_F64 storage");
+    if (p->mask != nullptr && !wide)
+      return fail(LBF_ENOTSUP, "two-component with walls needs LBF_F32 or LBF_F64 storage");
     if (!(p->width > 0.0) || !(p->sigma >= 0.0) || !(p->diffusivity >= 0.0))
       return fail(LBF_EINVAL, "need width > 0, sigma >= 0, diffusivity >= 0");
     if (p->force_field != nullptr) return fail(LBF_ENOTSUP, "two-component with a force field is not built");
   } else {
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(LBF_EINVAL, "tau must be > 0.5");
+    for (int a = 0; a < 3; ++a)
+      if (p->body_accel[a] != 0.0)
+        return fail(LBF_EINVAL, "body_accel is a two-component parameter (use force for a single component)");
   }
   return LBF_OK;
 }
+
+bool has_contrast(const lbf_params* p) { return p->two_component && p->rho_l != p->rho_h; }
 
 int grid_x(int nx, int xout = FwdTile<8>::XOUT) { return (nx + xout - 1) / xout; }
 int grid_y(int ny, int by) { return (ny + by - 1) / by; }
@@ -139,8 +146,9 @@ bool make_layout(const lbf_params* p, Layout* L) {
     L->F[0] = take(3 * N * cb);
     L->F[1] = take(3 * N * cb);
     L->G = take(3 * N * cb);
+    L->gphi = has_contrast(p) ? take(3 * N * cb) : 0;
   } else {
-    L->phi[0] = L->phi[1] = L->F[0] = L->F[1] = L->G = 0;
+    L->phi[0] = L->phi[1] = L->F[0] = L->F[1] = L->G = L->gphi = 0;
   }
   const long long gz = (p->nz + min_zchunk(p->nz) - 1) / min_zchunk(p->nz);
   // per-block partial sums of the largest grid either forward kernel can launch
@@ -181,6 +189,8 @@ struct lbf_ctx {
   void* phi[2];
   void* F[2];
   void* G;
+  void* gphi;      // density contrast: grad phi of the newest phase field
+  bool contrast;   // two components with rho_l != rho_h
   int pcur;
   double* partials;
   double* sums;       // 8 doubles at scal
@@ -211,7 +221,7 @@ struct lbf_ctx {
 
 namespace {
 
-KernelInfo forward_for(int Q, int storage, bool mask, bool two, bool field, bool tma, bool nearest) {
+KernelInfo forward_for(int Q, int storage, bool mask, int two, bool field, bool tma, bool nearest) {
   return forward_kernel_for(Q, storage, mask, two, field, tma, nearest);
 }
 
@@ -324,7 +334,13 @@ PhaseParams phase_params(const lbf_ctx* c) {
   pp.lambda = 4.0 * c->prm.diffusivity / c->prm.width;
   pp.beta = 12.0 * c->prm.sigma / c->prm.width;
   pp.kappa = 1.5 * c->prm.sigma * c->prm.width;
-  for (int a = 0; a < 3; ++a) pp.body[a] = c->prm.force[a];
+  for (int a = 0; a < 3; ++a) {
+    pp.body[a] = c->prm.force[a];
+    pp.accel[a] = c->prm.body_accel[a];
+  }
+  pp.rho_l = c->prm.rho_l;
+  pp.drho = c->prm.rho_h - c->prm.rho_l;
+  pp.mask = c->mask_d;
   pp.sc = c->sc;
   pp.zchunk = c->zchunk;
   return pp;
@@ -338,9 +354,9 @@ dim3 phase_grid(const lbf_ctx* c) {
 
 template <class T>
 void launch_forces_T(lbf_ctx* c, int which) {
-  k_phase_forces<T><<<phase_grid(c), phase_block(), 0, c->stream>>>(static_cast<const T*>(c->phi[which]),
-                                                                     static_cast<T*>(c->F[which]),
-                                                                     static_cast<T*>(c->G), phase_params(c));
+  k_phase_forces<T><<<phase_grid(c), phase_block(), 0, c->stream>>>(
+      static_cast<const T*>(c->phi[which]), static_cast<T*>(c->F[which]), static_cast<T*>(c->G),
+      c->contrast ? static_cast<T*>(c->gphi) : nullptr, phase_params(c));
 }
 
 void launch_forces(lbf_ctx* c, int which) {
@@ -378,6 +394,7 @@ FwdParams forward_params(const lbf_ctx* c, const void* src, void* dst, bool redu
     a.phi_new = c->phi[1 - c->pcur];
     a.F_old = c->F[c->pcur];
     a.F_new = c->F[1 - c->pcur];
+    a.grad_phi = c->gphi;
     a.rho_l = c->prm.rho_l;
     a.rho_h = c->prm.rho_h;
     a.nu_l = c->nu_l;
@@ -642,6 +659,8 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
     c->F[k] = c->two ? c->ws + L.F[k] : nullptr;
   }
   c->G = c->two ? c->ws + L.G : nullptr;
+  c->contrast = has_contrast(params);
+  c->gphi = c->contrast ? c->ws + L.gphi : nullptr;
   c->pcur = 0;
   c->partials = reinterpret_cast<double*>(c->ws + L.partials);
   c->sums = reinterpret_cast<double*>(c->ws + L.scal);
@@ -661,7 +680,8 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
 
   c->tma = tma_eligible(c->storage, c->nx);
   const bool nearest = params->rounding == LBF_ROUND_NEAREST;
-  c->fwd = forward_for(c->Q, c->storage, c->has_mask, c->two, params->force_field != nullptr, c->tma, nearest);
+  const int two_mode = c->two ? (c->contrast ? 2 : 1) : 0;
+  c->fwd = forward_for(c->Q, c->storage, c->has_mask, two_mode, params->force_field != nullptr, c->tma, nearest);
   c->fwd_tma30 = c->fwd;
   c->aligned = false;
   if (c->tma && !c->two && !c->pops && std::getenv("LBF_NO_ALIGNED") == nullptr) {
@@ -677,7 +697,7 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
     delete c;
     return fail(LBF_ENOTSUP, "no population kernel for this combination");
   }
-  c->fwd_direct = c->tma ? forward_for(c->Q, c->storage, c->has_mask, c->two, params->force_field != nullptr, false,
+  c->fwd_direct = c->tma ? forward_for(c->Q, c->storage, c->has_mask, two_mode, params->force_field != nullptr, false,
                                         params->rounding == LBF_ROUND_NEAREST)
                          : c->fwd;
   c->adj = adjoint_for(c->Q, c->storage, c->has_mask);
@@ -755,6 +775,8 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
         return cleanup(fail(LBF_ECUDA, "memset failed"));
     }
     if (cudaMemsetAsync(c->G, 0, 3 * c->N * cb, s) != cudaSuccess) return cleanup(fail(LBF_ECUDA, "memset failed"));
+    if (c->contrast && cudaMemsetAsync(c->gphi, 0, 3 * c->N * cb, s) != cudaSuccess)
+      return cleanup(fail(LBF_ECUDA, "memset failed"));
   }
   if (cudaStreamSynchronize(s) != cudaSuccess)
     return cleanup(fail(LBF_ECUDA, std::string("create: ") + cudaGetErrorString(cudaGetLastError())));
@@ -847,6 +869,20 @@ lbf_status lbf_set_moments(lbf_ctx* c, const void* src, int dt, const void* phi)
     }
     launch_forces(c, 0);
     LBF_CUDA(cudaGetLastError());
+    if (c->contrast) {  // the initial force also holds F^p + F^nu of the loaded state
+      const unsigned g = blocks_for(N, 256);
+      if (c->storage == LBF_F64)
+        k_contrast_init<double, double><<<g, 256, 0, s>>>(static_cast<const double*>(c->state[0]),
+                                                          static_cast<const double*>(c->phi[0]),
+                                                          static_cast<const double*>(c->gphi), static_cast<double*>(c->F[0]),
+                                                          N, c->prm.rho_h - c->prm.rho_l, c->nu_l, c->nu_h - c->nu_l);
+      else
+        k_contrast_init<float, float><<<g, 256, 0, s>>>(static_cast<const float*>(c->state[0]),
+                                                        static_cast<const float*>(c->phi[0]),
+                                                        static_cast<const float*>(c->gphi), static_cast<float*>(c->F[0]),
+                                                        N, c->prm.rho_h - c->prm.rho_l, c->nu_l, c->nu_h - c->nu_l);
+      LBF_CUDA(cudaGetLastError());
+    }
   }
   c->sums_valid = false;
   return LBF_OK;

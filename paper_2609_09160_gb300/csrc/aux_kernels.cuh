@@ -159,7 +159,10 @@ struct PhaseParams {
   int nx, ny, nz;
   long long N;
   double D, lambda, beta, kappa;
-  double body[3];
+  double body[3];    // body force per unit volume (part of F^b)
+  double accel[3];   // body acceleration a: F^b also holds rho(phi) a
+  double rho_l, drho;  // rho(phi) = rho_l + phi drho
+  const uint8_t* mask;  // solid sites (phi frozen, u = 0 there) or null
   Scales sc;
   int zchunk;
 };
@@ -213,6 +216,8 @@ struct PhaseColumn {
 // phi_new from phi, u (decoded from the state) and G, all at time n:
 //   phi' = phi - 3 sum_i w_i c_i . V(x + c_i) + 6 D sum_i w_i (phi(x + c_i) - phi(x)),
 //   V = phi u + lambda G
+// With walls, u is taken as 0 at solid sites and phi is not advanced there (it keeps its value),
+// so a wall in contact with one bulk phase exchanges no phi.
 template <class S, class T>
 __global__ void __launch_bounds__(PhaseTile<T>::SITES) k_phase_advance(const S* __restrict__ st,
                                                                        const T* __restrict__ phi,
@@ -243,6 +248,7 @@ __global__ void __launch_bounds__(PhaseTile<T>::SITES) k_phase_advance(const S* 
     rgx = G[s];
     rgy = G[N + s];
     rgz = G[2 * N + s];
+    if (p.mask != nullptr && p.mask[s]) rux = ruy = ruz = T(0);
   };
   auto take = [&](int k) {
     f[k] = rph;
@@ -267,7 +273,8 @@ __global__ void __launch_bounds__(PhaseTile<T>::SITES) k_phase_advance(const S* 
     if (c.out) {
       const T div = PT::dxay(sm[2] + me) + PT::dyax(sm[3] + me) + PT::axay(sm[4] + me);
       const T lap = PT::lap_xy(sm[0] + me) + PT::axay(sm[1] + me);
-      phi_new[(long long)z * plane + c.col] = f[1] - T(3) * div + dif6 * lap;
+      const long long s = (long long)z * plane + c.col;
+      phi_new[s] = (p.mask != nullptr && p.mask[s]) ? f[1] : f[1] - T(3) * div + dif6 * lap;
     }
     __syncthreads();
     f[0] = f[1];
@@ -283,11 +290,13 @@ __global__ void __launch_bounds__(PhaseTile<T>::SITES) k_phase_advance(const S* 
 
 // force F = mu grad phi + F^b and compression flux G from phi (time n+1):
 //   grad phi = 3 (D_x A_y A_z, D_y A_x A_z, D_z A_x A_y) phi, lap phi = 6 (A_x A_y A_z phi - phi),
-//   mu = 4 beta phi (phi - 1)(phi - 1/2) - kappa lap phi
+//   mu = 4 beta phi (phi - 1)(phi - 1/2) - kappa lap phi,  F^b = body + rho(phi) a.
+// With a density contrast grad phi is also written (gphi, else null): the fused step forms the
+// pressure and viscous-gradient forces from it and the raw moments of the new state.
 template <class T>
 __global__ void __launch_bounds__(PhaseTile<T>::SITES) k_phase_forces(const T* __restrict__ phi,
                                                                       T* __restrict__ F, T* __restrict__ G,
-                                                                      PhaseParams p) {
+                                                                      T* __restrict__ gphi, PhaseParams p) {
   using PT = PhaseTile<T>;
   __shared__ T sm[4][PT::SITES];  // A_z phi, D_z phi, phi, L_z phi of the current plane
   const PhaseColumn c(p);
@@ -295,6 +304,8 @@ __global__ void __launch_bounds__(PhaseTile<T>::SITES) k_phase_forces(const T* _
   const long long N = p.N, plane = (long long)p.nx * p.ny;
   const T beta4 = T(4) * T(p.beta), kappa = T(p.kappa);
   const T b0 = T(p.body[0]), b1 = T(p.body[1]), b2 = T(p.body[2]);
+  const T a0 = T(p.accel[0]), a1 = T(p.accel[1]), a2 = T(p.accel[2]);
+  const T rl = T(p.rho_l), dr = T(p.drho);
   auto fetch = [&](int zp) { return phi[(long long)wrap(zp, p.nz) * plane + c.col]; };  // zp in [-1, nz]
   T f0 = fetch(c.z0 - 1), f1 = fetch(c.z0), f2, nxt = fetch(c.z0 + 1);
   for (int z = c.z0; z < c.z1; ++z) {
@@ -310,9 +321,15 @@ __global__ void __launch_bounds__(PhaseTile<T>::SITES) k_phase_forces(const T* _
       const T lap = T(6) * (PT::lap_xy(sm[2] + me) + PT::axay(sm[3] + me));
       const T mu = beta4 * f1 * (f1 - T(1)) * (f1 - T(0.5)) - kappa * lap;
       const long long s = (long long)z * plane + c.col;
-      F[s] = mu * gx + b0;
-      F[N + s] = mu * gy + b1;
-      F[2 * N + s] = mu * gz + b2;
+      const T rho = rl + f1 * dr;
+      F[s] = mu * gx + (b0 + rho * a0);
+      F[N + s] = mu * gy + (b1 + rho * a1);
+      F[2 * N + s] = mu * gz + (b2 + rho * a2);
+      if (gphi != nullptr) {
+        gphi[s] = gx;
+        gphi[N + s] = gy;
+        gphi[2 * N + s] = gz;
+      }
       // phi (1 - phi) / max(|grad phi|, 1e-12)
       const T g2 = gx * gx + gy * gy + gz * gz;
       const T cc = f1 * (T(1) - f1) * rsqrt(g2 > T(1e-24) ? g2 : T(1e-24));
@@ -323,6 +340,25 @@ __global__ void __launch_bounds__(PhaseTile<T>::SITES) k_phase_forces(const T* _
     __syncthreads();
     f0 = f1;
     f1 = f2;
+  }
+}
+
+// Force of the initial state with a density contrast: F += F^p + F^nu from the stored p* and
+// N = A - u u (internal layout, FP32/FP64 storage), with grad rho = (rho_h - rho_l) grad phi:
+//   F^p = -p* cs2 grad rho,  F^nu = -(nu omega / cs2) N . grad rho,  nu = nu(phi), omega = 1/(nu/cs2 + 1/2)
+template <class S, class T>
+__global__ void k_contrast_init(const S* __restrict__ st, const T* __restrict__ phi, const T* __restrict__ gphi,
+                                T* __restrict__ F, long long N, double drho, double nu_l, double dnu) {
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
+    const T g0 = T(drho) * gphi[s], g1 = T(drho) * gphi[N + s], g2 = T(drho) * gphi[2 * N + s];
+    const T p3 = T(st[s]) * (T(1) / T(3));
+    const T nxx = T(st[4 * N + s]), nyy = T(st[5 * N + s]), nzz = T(st[6 * N + s]);
+    const T nxy = T(st[7 * N + s]), nxz = T(st[8 * N + s]), nyz = T(st[9 * N + s]);
+    const T nu = T(nu_l) + phi[s] * T(dnu);
+    const T cnu = T(-3) * nu / (T(3) * nu + T(0.5));
+    F[s] += -p3 * g0 + cnu * (nxx * g0 + nxy * g1 + nxz * g2);
+    F[N + s] += -p3 * g1 + cnu * (nxy * g0 + nyy * g1 + nyz * g2);
+    F[2 * N + s] += -p3 * g2 + cnu * (nxz * g0 + nyz * g1 + nzz * g2);
   }
 }
 

@@ -26,9 +26,9 @@ struct KernelInfo {
   bool store_map = false;  // the kernel also takes a tensor map of dst (TMA stores)
 };
 
-template <class L, class S, bool MASK, bool TWO, bool FF, bool TMA, bool RN>
+template <class L, class S, bool MASK, int TWO, bool FF, bool TMA, bool RN>
 KernelInfo fwd_info() {
-  constexpr int BY = fwd_rows_lattice(L::Q, int(sizeof(S)), MASK, TWO, L::HIGH);
+  constexpr int BY = fwd_rows_lattice(L::Q, int(sizeof(S)), MASK, TWO != 0, L::HIGH);
   KernelInfo k;
   k.fn = reinterpret_cast<const void*>(&k_stream_collide<L, S, BY, MASK, TWO, FF, TMA, RN>);
   k.smem = fwd_smem_bytes<L, S, BY, MASK, TMA>();
@@ -51,19 +51,34 @@ KernelInfo adj_info() {
   return k;
 }
 
-// forward kernel of lattice L and storage S for (mask, two-component, force field, TMA, 16-bit
-// round-to-nearest); fn == nullptr for combinations that are not built (two-component with a mask
-// or a force field). Round-to-nearest kernels exist for 16-bit storage only (FP32/FP64 stores
-// are exact).
+// forward kernel of lattice L and storage S for (mask, two-component mode, force field, TMA,
+// 16-bit round-to-nearest); two: 0 single component, 1 two components at equal densities, 2 with a
+// density contrast. fn == nullptr for combinations that are not built (two components with a force
+// field; a contrast or walls with two components in 16-bit storage). Round-to-nearest kernels exist
+// for 16-bit storage only (FP32/FP64 stores are exact).
 template <class L, class S, bool TMA, bool RN>
-KernelInfo forward_kernel_s(bool mask, bool two, bool field) {
-  if (two) return (mask || field) ? KernelInfo{nullptr, 0, 0, 0, 0} : fwd_info<L, S, false, true, false, TMA, RN>();
-  if (mask) return field ? fwd_info<L, S, true, false, true, TMA, RN>() : fwd_info<L, S, true, false, false, TMA, RN>();
-  return field ? fwd_info<L, S, false, false, true, TMA, RN>() : fwd_info<L, S, false, false, false, TMA, RN>();
+KernelInfo forward_kernel_s(bool mask, int two, bool field) {
+  constexpr bool wide = !Codec<S>::scaled;  // FP32 / FP64 storage
+  if (two != 0 && field) return KernelInfo{nullptr, 0, 0, 0, 0};
+  if (two == 2) {
+    if constexpr (wide)
+      return mask ? fwd_info<L, S, true, 2, false, TMA, RN>() : fwd_info<L, S, false, 2, false, TMA, RN>();
+    else
+      return KernelInfo{nullptr, 0, 0, 0, 0};
+  }
+  if (two == 1) {
+    if (!mask) return fwd_info<L, S, false, 1, false, TMA, RN>();
+    if constexpr (wide)
+      return fwd_info<L, S, true, 1, false, TMA, RN>();
+    else
+      return KernelInfo{nullptr, 0, 0, 0, 0};
+  }
+  if (mask) return field ? fwd_info<L, S, true, 0, true, TMA, RN>() : fwd_info<L, S, true, 0, false, TMA, RN>();
+  return field ? fwd_info<L, S, false, 0, true, TMA, RN>() : fwd_info<L, S, false, 0, false, TMA, RN>();
 }
 
 template <class L, class S>
-KernelInfo forward_kernel_ls(bool mask, bool two, bool field, bool tma, bool nearest) {
+KernelInfo forward_kernel_ls(bool mask, int two, bool field, bool tma, bool nearest) {
   if constexpr (Codec<S>::scaled) {
     if (nearest)
       return tma ? forward_kernel_s<L, S, true, true>(mask, two, field)
@@ -137,7 +152,7 @@ PopKernels pop_kernels_ls(bool mask, bool field) {
 
 // entry points implemented per (lattice, storage) translation unit
 #define LBF_DECLARE_TU(q, s)                                                             \
-  KernelInfo forward_kernel_q##q##_s##s(bool mask, bool two, bool field, bool tma, bool nearest); \
+  KernelInfo forward_kernel_q##q##_s##s(bool mask, int two, bool field, bool tma, bool nearest); \
   KernelInfo aligned_kernel_q##q##_s##s(bool mask, bool field, bool nearest);                    \
   PopKernels pop_kernels_q##q##_s##s(bool mask, bool field);                                        \
   KernelInfo adjoint_kernel_q##q##_s##s(bool mask);
@@ -156,7 +171,7 @@ LBF_DECLARE_TU(127, 3)
 #undef LBF_DECLARE_TU
 
 // lattice: 19 (D3Q19), 27 (D3Q27) or 127 (D3Q27h: D3Q27 with the complete Hermite basis)
-inline KernelInfo forward_kernel_for(int lattice, int storage, bool mask, bool two, bool field, bool tma,
+inline KernelInfo forward_kernel_for(int lattice, int storage, bool mask, int two, bool field, bool tma,
                                      bool nearest) {
   const bool q19 = lattice == 19;
   if (lattice == 127) {

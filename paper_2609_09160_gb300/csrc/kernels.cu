@@ -35,7 +35,7 @@ using TuS = __nv_bfloat16;
 #define LBF_CAT2(a, b, c, d) a##b##c##d
 #define LBF_CAT(a, b, c, d) LBF_CAT2(a, b, c, d)
 
-KernelInfo LBF_CAT(forward_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask, bool two, bool field, bool tma,
+KernelInfo LBF_CAT(forward_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask, int two, bool field, bool tma,
                                                                          bool nearest) {
   return forward_kernel_ls<TuL, TuS>(mask, two, field, tma, nearest);
 }

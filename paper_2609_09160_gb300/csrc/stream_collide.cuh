@@ -51,7 +51,8 @@ struct FwdParams {
   const void* phi_old;
   const void* phi_new;
   const void* F_old;
-  const void* F_new;
+  void* F_new;              // density contrast: read (F^s + F^b) and rewritten with the total force
+  const void* grad_phi;     // density contrast: grad phi^{n+1} [3][nz][ny][nx]
   double rho_l, rho_h, nu_l, nu_h;
   int nx, ny, nz;
   long long N;              // nx*ny*nz
@@ -434,13 +435,15 @@ constexpr size_t fwd_smem_bytes() {
          (MASK ? size_t(3) * (BY + 2) * 32 + 2 * kRingPad : 0);
 }
 
-// per-site inputs other than the 10 stored fields, prefetched one plane ahead
-template <class T, bool TWO>
+// per-site inputs other than the 10 stored fields, prefetched one plane ahead. TWO: 0 single
+// component, 1 two components at equal densities, 2 two components with a density contrast
+template <class T, int TWO>
 struct SiteExtra {
   T F[3];     // force at the site: uniform (+ field), or F^n for two components
   T phi_o;    // two components: phi^n (source side)
-  T Fn[3];    // two components: F^{n+1} (correction side)
+  T Fn[3];    // two components: F^{n+1} (correction side; with a contrast F^s + F^b only)
   T phi_n;    // two components: phi^{n+1}
+  T gphi[3];  // density contrast: grad phi^{n+1}
   bool solid;
 };
 
@@ -535,8 +538,8 @@ constexpr uint32_t kWaitPolls = 1u << 20;  // bound of every mbarrier wait
   } while (0)
 #endif
 
-template <class L, class S, int BY, bool MASK, bool TWO, bool FF, bool TMA, bool RN>
-__global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeof(S)), MASK, TWO))
+template <class L, class S, int BY, bool MASK, int TWO, bool FF, bool TMA, bool RN>
+__global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeof(S)), MASK, TWO != 0))
     k_stream_collide(const FwdParams a, const __grid_constant__ CUtensorMap tmap) {
   using T = typename ComputeOf<S>::type;
   using D = Dirs<L>;
@@ -637,9 +640,16 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
         const T* pn = static_cast<const T*>(a.phi_new) + zoff;
         const T* Fn = static_cast<const T*>(a.F_new) + zoff;
         e.phi_n = __ldg(pn + col);
-        e.Fn[0] = __ldg(Fn + col);
-        e.Fn[1] = __ldg(Fn + N + col);
-        e.Fn[2] = __ldg(Fn + 2 * N + col);
+        // F_new is rewritten by this kernel only at the site's own output, after this read
+        e.Fn[0] = Fn[col];
+        e.Fn[1] = Fn[N + col];
+        e.Fn[2] = Fn[2 * N + col];
+        if constexpr (TWO == 2) {
+          const T* gp = static_cast<const T*>(a.grad_phi) + zoff;
+          e.gphi[0] = __ldg(gp + col);
+          e.gphi[1] = __ldg(gp + N + col);
+          e.gphi[2] = __ldg(gp + 2 * N + col);
+        }
       }
     } else if constexpr (FF) {
       const T* fb = ffield + zoff;
@@ -684,11 +694,14 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
 
   // own-site values of the planes being output (carried from staging)
   T Fown[3] = {Fu0, Fu1, Fu2}, Fnext[3] = {Fu0, Fu1, Fu2};
-  // two components at equal densities: 1/(2 rho), and nu_l, nu_h - nu_l with the rate at nu_l
+  // two components: 1/(2 rho) at equal densities, rho_l and rho_h - rho_l with a contrast, and
+  // nu_l, nu_h - nu_l with the rate at nu_l
   const T i2r_two = TWO ? T(0.5) / pick<T>(a.rho_l, a.rho_l_f) : T(0.5);
+  const T rho_l_two = pick<T>(a.rho_l, a.rho_l_f), drho_two = pick<T>(a.rho_h - a.rho_l, a.drho_f);
   const T nu_l_two = pick<T>(a.nu_l, a.nu_l_f), dnu_two = pick<T>(a.nu_h - a.nu_l, a.dnu_f);
   const T omm_two = T(1) - T(1) / (T(3) * nu_l_two + T(0.5));
   T phi_own = T(0), phi_next = T(0);
+  T gphi_own[3] = {T(0), T(0), T(0)}, gphi_next[3] = {T(0), T(0), T(0)};
   // axial populations of the own column: up(z-1), up(z), dn(z), rest(z) and the new plane's
   T up_m1 = T(0), up_0 = T(0), dn_0 = T(0), rest_0 = T(0);
   T up_new = T(0), dn_new = T(0), rest_new = T(0);
@@ -709,9 +722,12 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     read_raw(p, kRawStages == 2 ? par : (p - pbase) % kRawStages, m);
     T inv2rho = T(0.5), omm = one_m_omega;
     if constexpr (TWO) {
-      // equal densities (the only two-component case built): 1/(2 rho) is a constant; the
-      // relaxation rate follows nu(phi) = nu_l + phi (nu_h - nu_l) when the phases differ
-      inv2rho = i2r_two;
+      // the source side takes rho(phi^n) and nu(phi^n) = nu_l + phi (nu_h - nu_l): at equal
+      // densities 1/(2 rho) is a constant, and the rate is a constant when the viscosities agree
+      if constexpr (TWO == 2)
+        inv2rho = T(0.5) / (rho_l_two + e.phi_o * drho_two);
+      else
+        inv2rho = i2r_two;
       if (dnu_two != T(0)) omm = T(1) - T(1) / (T(3) * (nu_l_two + e.phi_o * dnu_two) + T(0.5));
       else omm = omm_two;
       if (outcol) {
@@ -719,6 +735,11 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
         Fnext[0] = e.Fn[0];
         Fnext[1] = e.Fn[1];
         Fnext[2] = e.Fn[2];
+        if constexpr (TWO == 2) {
+          gphi_next[0] = e.gphi[0];
+          gphi_next[1] = e.gphi[1];
+          gphi_next[2] = e.gphi[2];
+        }
       }
     } else if constexpr (FF) {
       Fnext[0] = e.F[0];
@@ -842,6 +863,9 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   Fown[1] = Fnext[1];
   Fown[2] = Fnext[2];
   phi_own = phi_next;
+  gphi_own[0] = gphi_next[0];
+  gphi_own[1] = gphi_next[1];
+  gphi_own[2] = gphi_next[2];
   load_extra(z0 + 1, ex);
   if constexpr (MASK)
     any_0 = __syncthreads_or(any_0);
@@ -949,7 +973,30 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
         A = gather(std::false_type{});
       }
       // Eq. (corr): u = a1 + F/(2 rho), a2 = (sum c c f - cs2 a0 delta) + (u F + F u)/(2 rho)
-      const T i2r = i2r_two;
+      T i2r = i2r_two;
+      if constexpr (TWO == 2) {
+        // density contrast (Sec. 2 force split): the force of the new state adds to F^s + F^b
+        //   F^p = -p* cs2 grad rho and F^nu = -(nu omega / cs2) a*_neq . grad rho,
+        // with p* = a*0 and a*_neq = a*2 - a*1 a*1 the raw moments just streamed in (the
+        // uncorrected a*1), rho, nu, omega and grad rho = (rho_h - rho_l) grad phi at phi^{n+1}
+        const T rho_n = rho_l_two + phi_own * drho_two;
+        i2r = T(0.5) / rho_n;
+        const T gr0 = drho_two * gphi_own[0], gr1 = drho_two * gphi_own[1], gr2 = drho_two * gphi_own[2];
+        const T p3 = A.a0 * (T(1) / T(3));
+        const T qxx = (A.rxx - p3) - A.jx * A.jx, qyy = (A.ryy - p3) - A.jy * A.jy, qzz = (A.rzz - p3) - A.jz * A.jz;
+        const T qxy = A.rxy - A.jx * A.jy, qxz = A.rxz - A.jx * A.jz, qyz = A.ryz - A.jy * A.jz;
+        const T nu_n = nu_l_two + phi_own * dnu_two;
+        const T cnu = T(-3) * nu_n / (T(3) * nu_n + T(0.5));
+        Fown[0] += -p3 * gr0 + cnu * (qxx * gr0 + qxy * gr1 + qxz * gr2);
+        Fown[1] += -p3 * gr1 + cnu * (qxy * gr0 + qyy * gr1 + qyz * gr2);
+        Fown[2] += -p3 * gr2 + cnu * (qxz * gr0 + qyz * gr1 + qzz * gr2);
+        if (outcol && !sol_0) {
+          T* Fw = static_cast<T*>(a.F_new) + (long long)z * plane + col;
+          Fw[0] = Fown[0];
+          Fw[N] = Fown[1];
+          Fw[2 * N] = Fown[2];
+        }
+      }
       const T hx = (SITEF ? Fown[0] : Fu0) * i2r, hy = (SITEF ? Fown[1] : Fu1) * i2r,
               hz = (SITEF ? Fown[2] : Fu2) * i2r;
       const T ux = A.jx + hx, uy = A.jy + hy, uz = A.jz + hz;
@@ -1003,6 +1050,9 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     Fown[1] = Fnext[1];
     Fown[2] = Fnext[2];
     phi_own = phi_next;
+    gphi_own[0] = gphi_next[0];
+    gphi_own[1] = gphi_next[1];
+    gphi_own[2] = gphi_next[2];
     any_m = any_0;
     any_0 = any_p;
     const int g2t = g2m;

@@ -28,7 +28,8 @@ class Solver:
     storage 'f64' | 'f32' | 'f16' | 'bf16'.
     force: uniform 3-vector; force_field: CUDA tensor (3, nz, ny, nx) in the compute dtype
     (float64 for 'f64' storage, else float32), kept by reference; mask: bool/uint8 (nz, ny, nx),
-    nonzero = solid. two_component: dict(rho_l, rho_h, tau_l, tau_h, sigma, width, diffusivity).
+    nonzero = solid. two_component: dict(rho_l, rho_h, tau_l, tau_h, sigma, width, diffusivity and
+    optionally body_accel, a uniform body acceleration).
     """
 
     def __init__(self, shape, lattice=19, tau=0.8, storage="f32", force=(0.0, 0.0, 0.0), force_field=None,
@@ -67,6 +68,8 @@ class Solver:
             p.rho_l, p.rho_h = float(tc.get("rho_l", 1.0)), float(tc.get("rho_h", 1.0))
             p.tau_l, p.tau_h = float(tc["tau_l"]), float(tc["tau_h"])
             p.sigma, p.width, p.diffusivity = float(tc["sigma"]), float(tc["width"]), float(tc["diffusivity"])
+            for k, v in enumerate(tc.get("body_accel", (0.0, 0.0, 0.0))):
+                p.body_accel[k] = float(v)
         if scale_hint is not None:
             for a in range(3):
                 p.scale_hint[a] = float(scale_hint[a])

@@ -119,8 +119,9 @@ def test_workspace_holds_two_moment_buffers(lib):
     (dict(populations=1, storage=_lbf.LBF_F16), _lbf.LBF_ENOTSUP),
     (dict(populations=1, two_component=1, tau_l=1.0, tau_h=1.0, rho_l=1.0, rho_h=1.0, width=4.0, sigma=0.03,
           diffusivity=0.1), _lbf.LBF_ENOTSUP),
-    (dict(two_component=1, tau_l=1.0, tau_h=1.0, rho_l=0.5, rho_h=1.5, width=4.0, sigma=0.03, diffusivity=0.1),
-     _lbf.LBF_ENOTSUP),
+    (dict(two_component=1, tau_l=1.0, tau_h=1.0, rho_l=0.5, rho_h=1.5, width=4.0, sigma=0.03, diffusivity=0.1,
+          storage=_lbf.LBF_F16), _lbf.LBF_ENOTSUP),
+    (dict(body_accel=(0.0, 0.0, 1e-6)), _lbf.LBF_EINVAL),
     (dict(two_component=1, tau_l=1.0, tau_h=0.4, rho_l=1.0, rho_h=1.0, width=4.0, sigma=0.03, diffusivity=0.1),
      _lbf.LBF_EINVAL),
 ])
@@ -136,6 +137,11 @@ def test_valid_parameters(lib):
     for lattice in (_lbf.LBF_D3Q19, _lbf.LBF_D3Q27, _lbf.LBF_D3Q27H):
         for storage in (_lbf.LBF_F64, _lbf.LBF_F32, _lbf.LBF_F16, _lbf.LBF_BF16):
             assert _lbf.lbf_validate(params(lattice=lattice, storage=storage)) == _lbf.LBF_OK
+    # density contrast (FP32/FP64): one more 3-vector field (grad phi) than equal densities
+    tc = dict(two_component=1, tau_l=1.0, tau_h=0.8, rho_l=1.0, rho_h=1.0, width=4.0, sigma=0.03, diffusivity=0.1)
+    eq = _lbf.lbf_workspace_bytes(params(**tc))
+    ctr = _lbf.lbf_workspace_bytes(params(**dict(tc, rho_h=2.0, body_accel=(0.0, 1e-6, 0.0))))
+    assert eq > 0 and ctr - eq >= 3 * 16 ** 3 * 4
     # D3Q27h keeps the 10-field state: same workspace as D3Q27
     assert _lbf.lbf_workspace_bytes(params(lattice=_lbf.LBF_D3Q27H)) == _lbf.lbf_workspace_bytes(params(lattice=27))
     tc = params(two_component=1, tau_l=1.0, tau_h=0.8, rho_l=1.0, rho_h=1.0, width=4.0, sigma=0.03, diffusivity=0.1)

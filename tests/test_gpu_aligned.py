@@ -54,9 +54,13 @@ def test_aligned_kernel_matches_30_column_kernel(lattice, storage, kind):
             s.step(3)
         err = group_errors(a.moments(), b.moments())
         assert max(err.values()) < ULPS[storage], (shape, err)
+        # the sums add the computed values; in 16-bit storage the states they come from differ by
+        # the rounding of a few values, so the bound scales with the sum of magnitudes
         ra, rb = a.reduce(), b.reduce()
+        mag = [M0[0].abs().sum().item()] + [M0[1 + i].abs().sum().item() for i in range(3)]
+        mag += [1.0, (M0[1:4] ** 2).sum().item()]
         for k in (0, 1, 2, 3, 5):
-            assert abs(ra[k] - rb[k]) <= 1e-5 * max(1.0, abs(rb[k])), (k, ra[k], rb[k])
+            assert abs(ra[k] - rb[k]) <= ULPS[storage] * max(1.0, mag[k]), (k, ra[k], rb[k])
 
 
 @pytest.mark.parametrize("lattice", [19, 27])
