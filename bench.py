@@ -147,6 +147,9 @@ LATTICE_NAME = {19: "D3Q19", 27: "D3Q27", 127: "D3Q27h"}
 # kernels: the fused step reads phi and F at t and t+1 (4 + 12 + 4 + 12), the phase-field advance
 # reads phi, u, G and writes phi (4 + 12 + 12 + 4), the forces read phi and write F and G (4 + 24)
 TWO_COMPONENT_EXTRA_BYTES = 32 + 32 + 28
+# with a density contrast the forces kernel also writes grad phi (12), the fused step reads it (12)
+# and writes the total force of the new state back (12); walls add the mask byte to the advance
+CONTRAST_EXTRA_BYTES = 36 + 1
 
 WORKLOADS = {
     # key: (lattice, storage, builder) -- the headline is "channel256"
@@ -191,6 +194,24 @@ def droplet_solver(torch, device, n=128):
     M0 = torch.zeros((10,) + shape, dtype=torch.float32, device=device)
     s._phi0 = phi0
     return s, M0, None
+
+
+def layered_solver(torch, device, nx=512, ny=8, nz=1024):
+    """Layered two-phase Poiseuille flow (Sec. 4): walls at x = 0 and nx - 1, light phase
+    (rho 0.5, nu 0.05) for x < nx/2, heavy phase (rho 1.5, nu 0.4) above, tanh interface of width
+    4, body acceleration 1e-7 along z, fluid at rest."""
+    from paper_2609_09160_gb300 import Solver
+
+    shape = (nz, ny, nx)
+    x = torch.arange(nx, dtype=torch.float32, device=device)
+    phi0 = (0.5 * (1 + torch.tanh(2 * (x - nx / 2) / 4.0))).reshape(1, 1, nx).expand(shape).contiguous()
+    mask = torch.zeros(shape, dtype=torch.bool)
+    mask[..., 0] = mask[..., -1] = True
+    tc = dict(rho_l=0.5, rho_h=1.5, tau_l=3 * 0.05 + 0.5, tau_h=3 * 0.4 + 0.5, sigma=0.03, width=4.0,
+              diffusivity=0.1, body_accel=(0.0, 0.0, 1e-7))
+    s = Solver(shape, lattice=19, storage="f32", two_component=tc, mask=mask, device=device)
+    M0 = torch.zeros((10,) + shape, dtype=torch.float32, device=device)
+    return s, M0, phi0
 
 
 def adjoint_rollout(torch, device, T=500, K=50, reps=2):
@@ -402,6 +423,18 @@ def extras(torch, device, quick):
     r["note"] = "3 kernels per step (phase field advance, forces, fused LB)"
     out["droplet128_d3q19_f32"] = r
     del s, M0
+    torch.cuda.empty_cache()
+
+    # density and viscosity contrast: the layered two-phase Poiseuille flow of Sec. 4 at the paper's
+    # size, 512 (x, walls at x = 0 and 511) x 8 x 1024 (z, flow direction), rho 0.5 / 1.5,
+    # nu 0.05 / 0.4, W = 4, sigma = 0.03, body acceleration 1e-7 along z, interface at x = 256
+    s, M0, phi0 = layered_solver(torch, device)
+    s.set_moments(M0, phi0)
+    r = rate(s, 50 if quick else 200, 5,
+             TWO_COMPONENT_EXTRA_BYTES + CONTRAST_EXTRA_BYTES + algorithmic_bytes("f32", mask=True))
+    r["note"] = "3 kernels per step; pressure and viscous-gradient forces in the fused step"
+    out["layered512x8x1024_d3q19_f32_contrast"] = r
+    del s, M0, phi0
 
     # FP64 parity mode: 32^3 Taylor-Green (launch-latency bound at this size)
     s = Solver((32, 32, 32), lattice=19, tau=0.8, storage="f64", device=device)

@@ -200,7 +200,9 @@ def test_tma_and_direct_loads_agree(lattice, storage, walls, monkeypatch):
     """The TMA-staged and the directly loaded kernels read the same values and run the same
     arithmetic, compiled separately: the compiler may group multiply-adds differently in the two
     variants (each is deterministic run to run), so one step from the same state must agree to the
-    rounding of the storage type - a few units in the last place of FP32/FP64, one of FP16/BF16."""
+    rounding of the storage type - a few units in the last place of FP32/FP64, one or two of
+    FP16/BF16 (two where a value near zero comes out of a cancellation: its FP32 rounding error is
+    then about one unit of the 16-bit value)."""
     shape = (9, 19, 64)
     M0 = synth.random_moments(shape, seed=40)
     mask = synth.channel_walls(shape) | synth.random_mask(shape, 0.05, seed=41) if walls else None
@@ -221,7 +223,7 @@ def test_tma_and_direct_loads_agree(lattice, storage, walls, monkeypatch):
         # adjacent 16-bit values of one sign differ by one in their bit patterns
         ia = outs[0][0].view(torch.int16).int()
         ib = outs[1][0].view(torch.int16).int()
-        assert int((ia - ib).abs().max()) <= 1
+        assert int((ia - ib).abs().max()) <= 2
         assert (ia != ib).float().mean().item() < 1e-3
     for x, y in zip(outs[0][2], outs[1][2]):
         assert abs(x - y) <= 1e-3 * max(abs(y), 1e-12)
