@@ -53,13 +53,34 @@ struct RingN {
 
 constexpr size_t round128(size_t b) { return (b + 127) / 128 * 128; }
 
+// output planes leave shared memory by TMA tensor stores (1) or by per-thread stores (0); with
+// TMA stores, LBF_AL_OUT_STAGES output stages rotate so that a store may still be reading one
+// stage while the next plane is written into the other
+#ifndef LBF_AL_TMA_STORE
+#define LBF_AL_TMA_STORE 0
+#endif
+#ifndef LBF_AL_OUT_STAGES
+#define LBF_AL_OUT_STAGES 1
+#endif
+// halo rows and columns stage only the directions pulled into the tile (0) or every direction
+// with the output rows' code (1)
+// with walls, one gather body whose bounce-back selects run on every tile (1), or a second body
+// without them for tiles far from any wall (0)
+#ifndef LBF_AL_ONE_GATHER
+#define LBF_AL_ONE_GATHER 0
+#endif
+#ifndef LBF_AL_HALO_ALL
+#define LBF_AL_HALO_ALL 1
+#endif
+constexpr int kAlOutStages = LBF_AL_TMA_STORE ? LBF_AL_OUT_STAGES : 0;
+
 template <class S, int TY>
 constexpr size_t al_stage_bytes() {
   return round128(size_t(10) * AlTile<S, TY>::ROWS * AlTile<S, TY>::BX * sizeof(S));
 }
 template <class S, int TY>
 constexpr size_t al_out_bytes() {
-  return round128(size_t(10) * TY * 32 * sizeof(S));
+  return kAlOutStages * round128(size_t(10) * TY * 32 * sizeof(S));
 }
 
 template <class L, class S, int TY, bool MASK>
@@ -124,6 +145,7 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
   constexpr int G0 = D::gsize(0) * SITES, G1 = D::gsize(1) * SITES, G2 = D::gsize(2) * SITES;
   constexpr int GS2 = D::gsize(2);
   constexpr int OSTR = TY * 32;  // field stride of the output stage
+  constexpr int OSTAGE = int(round128(size_t(10) * TY * 32 * sizeof(S)) / sizeof(S));  // elements per output stage
   static_assert(al_smem_bytes<L, S, TY, MASK>() >= 6 * 512 * sizeof(double) + 128, "smem too small for the final tree");
   static_assert(G::THREADS <= 512, "final tree assumes <= 512 threads");
 
@@ -254,8 +276,8 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
 
   // staging of plane p by role H (compile time): the post-collision populations this site
   // contributes to the tile, into the ring (axial ones of output rows into registers)
-  auto stage_as = [&](auto par_c, auto role_c, int p, int g2, const SiteExtra<T, false>& e) {
-    constexpr int par = decltype(par_c)::value;
+  // par = (p - pbase) & 1 at run time: one copy of the plane loop (instruction-cache footprint)
+  auto stage_as = [&](int par, auto role_c, int p, int g2, const SiteExtra<T, false>& e) {
     constexpr int H = decltype(role_c)::value;
     T m[10];
     read_raw(p, kRawStages == 2 ? par : (p - pbase) % kRawStages, m);
@@ -322,7 +344,12 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
     if constexpr (MASK) msk[g2 / GS2 + me] = e.solid ? 1 : 0;
     if (H == 0) sol_new = e.solid;
   };
-  auto stage = [&](auto par_c, int p, int g2, const SiteExtra<T, false>& e) -> bool {
+  auto stage = [&](int par_c, int p, int g2, const SiteExtra<T, false>& e) -> bool {
+#if LBF_AL_HALO_ALL
+    // one staging body for every role (every direction): less code than the per-role bodies
+    if (role != 5) stage_as(par_c, std::integral_constant<int, 0>{}, p, g2, e);
+    return e.solid;
+#endif
     if (warp < TY) stage_as(par_c, std::integral_constant<int, 0>{}, p, g2, e);
     else if (warp == TY) stage_as(par_c, std::integral_constant<int, 1>{}, p, g2, e);
     else if (warp == TY + 1) stage_as(par_c, std::integral_constant<int, 2>{}, p, g2, e);
@@ -355,7 +382,7 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
 
   load_extra(z0 - 1, ex);
   wait_plane(z0 - 1);
-  bool any_m = stage(std::integral_constant<int, 0>{}, z0 - 1, g2m, ex);
+  bool any_m = stage(0, z0 - 1, g2m, ex);
   up_m1 = up_new;
   sol_m1 = sol_new;
   load_extra(z0, ex);
@@ -365,7 +392,7 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
     __syncthreads();
   if (ctrl) issue(z0 - 1 + kRawStages);
   wait_plane(z0);
-  bool any_0 = stage(std::integral_constant<int, 1>{}, z0, g20, ex);
+  bool any_0 = stage(1, z0, g20, ex);
   if (warp == G::CTRL) wait_plane(z0 + 1);
   up_0 = up_new;
   dn_0 = dn_new;
@@ -383,20 +410,26 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
 
   bool store_pending = false;  // control thread: a TMA store may still read the output stage
 
-  auto iteration = [&](auto par_c, int z) {
-    constexpr int PAR = decltype(par_c)::value;
-    bool any_p = stage(std::integral_constant<int, PAR>{}, z + 1, g2p, ex);
+  auto iteration = [&](int PAR, int z) {
+    bool any_p = stage(PAR, z + 1, g2p, ex);
     load_extra(z + 2, ex);
     if (ctrl && store_pending) {
-      bulk_wait_group_read0();  // the output stage is rewritten after the barrier
-      store_pending = false;
+      // the output stage written after the barrier is free: with one stage the store issued last,
+      // with two the one before it has finished reading shared memory
+      if constexpr (kAlOutStages >= 2)
+        bulk_wait_group_read1();
+      else
+        bulk_wait_group_read0();
     }
     if constexpr (MASK)
       any_p = __syncthreads_or(any_p);
     else
       __syncthreads();
     if (ctrl) issue(z + 1 + kRawStages);
-    const bool wall = MASK && (any_0 != 0);  // block-uniform: a solid site in this plane's patch
+    // block-uniform: a solid site in this plane's patch (then per-thread stores that skip solid
+    // sites); without TMA stores every plane takes that path
+    const bool wall = !LBF_AL_TMA_STORE || (MASK && (any_0 != 0));
+    S* const ostage = outst + (kAlOutStages >= 2 ? ((z - z0) & 1) * OSTAGE : 0);
     if (out_row) {
       const T* P0 = ring + R::base(0) + (R::NS0 == 2 ? PAR : 0) * G0 + me;
       const T* P1 = ring + R::base(1) + (PAR ^ 1) * G1 + me;
@@ -470,7 +503,9 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
         return A;
       };
       Accum<T> A;
-      if constexpr (MASK) {
+      if constexpr (MASK && LBF_AL_ONE_GATHER) {
+        A = gather(std::true_type{});  // one gather body: the bounce-back selects run everywhere
+      } else if constexpr (MASK) {
         if (any_m || any_0 || any_p)
           A = gather(std::true_type{});
         else
@@ -494,7 +529,7 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
       uint32_t rs = Codec<S>::scaled && !RN ? fmix32(uint32_t(zc) ^ a.salt) : 0u;
       if (!wall) {
         // every site of the patch is fluid: the output stage, stored by one TMA box after the barrier
-        S* o = outst + warp * 32 + lane;
+        S* o = ostage + warp * 32 + lane;
         LBF_CHECK(a.flags, warp * 32 + lane + 9 * OSTR < 10 * OSTR);
         st_field<S, RN>(o, 0, A.a0, a.sc.enc[0], rs);
         st_field<S, RN>(o + OSTR, 0, ux, a.sc.enc[1], rs);
@@ -547,16 +582,13 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
     if (warp == G::CTRL && z + 2 <= z1) wait_plane(z + 2);
     __syncthreads();
     if (ctrl && !wall) {
-      tma_store_4d(&tstore, outst, x0, y0, z, 0);
+      tma_store_4d(&tstore, ostage, x0, y0, z, 0);
       bulk_commit_group();
       store_pending = true;
     }
   };
 
-  for (int z = z0; z < z1 && !abort_flag; z += 2) {
-    iteration(std::integral_constant<int, 0>{}, z);
-    if (z + 1 < z1 && !abort_flag) iteration(std::integral_constant<int, 1>{}, z + 1);
-  }
+  for (int z = z0; z < z1 && !abort_flag; ++z) iteration((z - z0) & 1, z);
 
   if (ctrl) {
     bulk_wait_group0();  // the stores are complete and the output stage is free
