@@ -61,7 +61,7 @@ size_t storage_bytes(int storage) {
 size_t compute_bytes(int storage) { return storage == LBF_F64 ? 8 : 4; }
 
 struct Layout {
-  size_t state[2], mom, mask, phi[2], F[2], G, gphi, partials, scal, staging, total;
+  size_t state[2], mom, mask, walls, phi[2], F[2], G, gphi, partials, scal, staging, total;
   long long npartials;
   size_t staging_bytes;
 };
@@ -156,6 +156,7 @@ bool make_layout(const lbf_params* p, Layout* L) {
   if (const int aby = aligned_by(p)) tiles = std::max(tiles, (long long)grid_x(p->nx, 32) * grid_y(p->ny, aby));
   L->npartials = std::max<long long>(tiles * gz, 1024);
   L->partials = take(size_t(L->npartials) * 8 * sizeof(double));
+  L->walls = p->mask ? take(size_t(L->npartials)) : 0;  // one byte per CTA: its patch holds a solid site
   L->scal = take(64 * sizeof(double));
   L->staging_bytes = std::min<size_t>(kStagingMax, size_t(11) * 8 * size_t(N));
   L->staging = take(L->staging_bytes);
@@ -209,6 +210,8 @@ struct lbf_ctx {
   bool aligned;         // the forward kernel is the line-aligned one (TMA loads and stores)
   CUtensorMap tmap[2];  // tensor maps of the two state buffers (TMA source)
   CUtensorMap smap[2];  // tensor maps of the two state buffers (TMA store destination)
+  uint8_t* walls_d;     // per-CTA flag of the row-synchronised kernel: a solid site in its patch
+  std::vector<uint8_t> walls_h;
   bool sums_valid;
   bool unstable_seen;
   double omega, nu_l, nu_h;
@@ -500,6 +503,7 @@ lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
       k = &c->fwd_direct;
     }
   } else if (c->tma) {
+    const int box_y = k->by + 2;
     if (src == c->state[0]) {
       tm = c->tmap[0];
     } else if (src == c->state[1]) {
@@ -507,11 +511,12 @@ lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
     } else if (!aligned16) {
       k = &c->fwd_direct;
     } else {
-      lbf_status st = encode_state_map(c, src, &tm, k->box_x, k->by + 2);
+      lbf_status st = encode_state_map(c, src, &tm, k->box_x, box_y);
       if (st != LBF_OK) return st;
     }
   }
-  void* args[] = {&a, &tm, &sm};
+  const uint8_t* walls = c->walls_d;
+  void* args[] = {&a, &tm, k->row_boxes ? static_cast<void*>(&walls) : static_cast<void*>(&sm)};
   const dim3 grid(grid_x(c->nx, k->xout), grid_y(c->ny, k->by), c->fgrid.z);
   LBF_CUDA(cudaLaunchKernel(k->fn, grid, dim3(32, k->threads / 32, 1), args, k->smem, c->stream));
   return LBF_OK;
@@ -684,12 +689,19 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   c->fwd = forward_for(c->Q, c->storage, c->has_mask, two_mode, params->force_field != nullptr, c->tma, nearest);
   c->fwd_tma30 = c->fwd;
   c->aligned = false;
-  if (c->tma && !c->two && !c->pops && std::getenv("LBF_NO_ALIGNED") == nullptr) {
+  // single-component TMA steps: the row-synchronised kernel, or (LBF_KERNEL=aligned / cta) the
+  // line-aligned kernel or the CTA-synchronised one
+  const char* kind = std::getenv("LBF_KERNEL");
+  const std::string kname = kind ? kind : "rows";
+  if (c->tma && !c->two && !c->pops && kname == "aligned") {
     const KernelInfo al = aligned_kernel_for(c->Q, c->storage, c->has_mask, params->force_field != nullptr, nearest);
     if (al.fn != nullptr) {
       c->fwd = al;
       c->aligned = true;
     }
+  } else if (c->tma && !c->two && !c->pops && kname == "rows") {
+    const KernelInfo rk = rows_kernel_for(c->Q, c->storage, c->has_mask, params->force_field != nullptr, nearest);
+    if (rk.fn != nullptr) c->fwd = rk;
   }
   c->popk = c->pops ? pop_kernels_for(c->Q, c->storage, c->has_mask, params->force_field != nullptr)
                     : PopKernels{nullptr, nullptr, nullptr};
@@ -766,6 +778,30 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   if (c->has_mask) {
     if (cudaMemcpyAsync(c->mask_d, params->mask, c->N, cudaMemcpyHostToDevice, s) != cudaSuccess)
       return cleanup(fail(LBF_ECUDA, "mask copy failed"));
+    // per-CTA walls table of the row-synchronised kernel: does the patch it reads (planes
+    // z0 - 1 .. z1, rows y0 - 1 .. y0 + by, columns x0 - 1 .. x0 + 30, periodic) hold a solid site
+    if (c->fwd.row_boxes) {
+      c->walls_d = reinterpret_cast<uint8_t*>(c->ws + L.walls);
+      c->walls_h.assign(size_t(forward_blocks(c)), 0);
+      const int by = c->fwd.by, xo = c->fwd.xout;
+      const uint8_t* m = params->mask;
+      for (unsigned bz = 0; bz < c->fgrid.z; ++bz)
+        for (unsigned byi = 0; byi < c->fgrid.y; ++byi)
+          for (unsigned bx = 0; bx < c->fgrid.x; ++bx) {
+            const int z0 = int(bz) * c->zchunk, z1 = std::min(c->nz, z0 + c->zchunk);
+            bool any = false;
+            for (int z = z0 - 1; z <= z1 && !any; ++z)
+              for (int y = int(byi) * by - 1; y <= int(byi) * by + by && !any; ++y)
+                for (int x = int(bx) * xo - 1; x <= int(bx) * xo + xo && !any; ++x) {
+                  const int zz = (z % c->nz + c->nz) % c->nz, yy = (y % c->ny + c->ny) % c->ny,
+                            xx = (x % c->nx + c->nx) % c->nx;
+                  any = m[((long long)zz * c->ny + yy) * c->nx + xx] != 0;
+                }
+            c->walls_h[(size_t(bz) * c->fgrid.y + byi) * c->fgrid.x + bx] = any ? 1 : 0;
+          }
+      if (cudaMemcpyAsync(c->walls_d, c->walls_h.data(), c->walls_h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return cleanup(fail(LBF_ECUDA, "walls table copy failed"));
+    }
   }
   if (c->two) {
     const size_t cb = compute_bytes(c->storage);
