@@ -102,11 +102,15 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   const bool walls = MASK && (tile_walls == nullptr || tile_walls[cta] != 0);  // block-uniform
 
   // bounded wait on a phase parity, warp-uniform (every lane polls, the warp leaves together);
-  // gives up on time-out, or when another row has aborted
+  // gives up on time-out, or when another row has aborted. The non-blocking test is used with a
+  // short sleep between polls: a potentially blocking try_wait can suspend the warp for far
+  // longer than a neighbour row needs to arrive, and a hot spin takes issue slots from the rows
+  // doing the work.
   auto wait_bar = [&](uint64_t* bar, uint32_t parity) -> bool {
     for (uint32_t i = 0; i < kWaitPolls; ++i) {
-      const bool ok = mbar_try_wait(bar, parity);
+      const bool ok = mbar_test_wait(bar, parity);
       if (__all_sync(0xffffffffu, ok)) return true;
+      __nanosleep(32);
       if ((i & 63u) == 63u && __any_sync(0xffffffffu, abort_flag != 0)) return false;
     }
     if (lane == 0) {
