@@ -40,6 +40,24 @@ struct AdjParams {
   int zchunk;
 };
 
+// adds the pair (g_q, g_opp(q)) of direction c with weight w like accumulate_pair, but the diagonal
+// second moments directly in traceless form, sum w (c_a c_a - 1/3) s: an adjoint field with a large
+// isotropic part would otherwise lose its traceless part to the cancellation sum w c_a^2 s - a0 / 3
+template <int cx, int cy, int cz, class T>
+__device__ __forceinline__ void accumulate_pair_traceless(Accum<T>& A, T gq, T go, T w) {
+  const T s = gq + go, d = gq - go;
+  A.a0 = fma(w, s, A.a0);
+  A.jx = sfma<cx>(A.jx, w, d);
+  A.jy = sfma<cy>(A.jy, w, d);
+  A.jz = sfma<cz>(A.jz, w, d);
+  A.rxx = fma(w * T(cx * cx * 3 - 1) * T(1.0 / 3.0), s, A.rxx);
+  A.ryy = fma(w * T(cy * cy * 3 - 1) * T(1.0 / 3.0), s, A.ryy);
+  A.rzz = fma(w * T(cz * cz * 3 - 1) * T(1.0 / 3.0), s, A.rzz);
+  A.rxy = sfma<cx * cy>(A.rxy, w, s);
+  A.rxz = sfma<cx * cz>(A.rxz, w, s);
+  A.ryz = sfma<cy * cz>(A.ryz, w, s);
+}
+
 template <class L, class S, int BY, bool MASK>
 __global__ void __launch_bounds__(FwdTile<BY>::THREADS)
     k_adjoint(const AdjParams a) {
@@ -173,6 +191,10 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS)
         Accum<T> A = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         const T* base0 = nus + s_0 * PLANE + me;
         A.a0 = T(L::w(REST)) * base0[REST * ROWS * 32];
+        // the rest population's share of the traceless diagonal: w_0 (0 - 1/3) nu_0
+        A.rxx = A.a0 * T(-1.0 / 3.0);
+        A.ryy = A.rxx;
+        A.rzz = A.rxx;
         static_for<Q>([&](auto qc) {
           constexpr int q = decltype(qc)::value;
           if constexpr (q != REST && q < L::opp(q)) {
@@ -191,14 +213,12 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS)
                 if (msk[slot_o * ROWS * 32 + me + off_o]) go = base0[q * ROWS * 32];
               }
             }
-            accumulate_pair<cx, cy, cz, T>(A, gq, go, T(L::w(q)));
+            accumulate_pair_traceless<cx, cy, cz, T>(A, gq, go, T(L::w(q)));
           }
         });
-        const T third = T(1) / T(3);
         const T pi0 = A.a0;
         const T p1x = T(3) * A.jx, p1y = T(3) * A.jy, p1z = T(3) * A.jz;
-        const T a0c = A.a0 * third;
-        const T qxx = T(4.5) * (A.rxx - a0c), qyy = T(4.5) * (A.ryy - a0c), qzz = T(4.5) * (A.rzz - a0c);
+        const T qxx = T(4.5) * A.rxx, qyy = T(4.5) * A.ryy, qzz = T(4.5) * A.rzz;
         const T qxy = T(4.5) * A.rxy, qxz = T(4.5) * A.rxz, qyz = T(4.5) * A.ryz;
         const T ux = ld_field<S, T>(st0, N + site, a.sc.dec[1]);
         const T uy = ld_field<S, T>(st0, 2 * N + site, a.sc.dec[1]);

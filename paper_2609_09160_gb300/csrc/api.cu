@@ -61,7 +61,7 @@ size_t storage_bytes(int storage) {
 size_t compute_bytes(int storage) { return storage == LBF_F64 ? 8 : 4; }
 
 struct Layout {
-  size_t state[2], mom, mask, walls, phi[2], F[2], G, gphi, partials, scal, staging, total;
+  size_t state[2], mom, mask, phi[2], F[2], G, gphi, partials, scal, staging, total;
   long long npartials;
   size_t staging_bytes;
 };
@@ -156,7 +156,6 @@ bool make_layout(const lbf_params* p, Layout* L) {
   if (const int aby = aligned_by(p)) tiles = std::max(tiles, (long long)grid_x(p->nx, 32) * grid_y(p->ny, aby));
   L->npartials = std::max<long long>(tiles * gz, 1024);
   L->partials = take(size_t(L->npartials) * 8 * sizeof(double));
-  L->walls = p->mask ? take(size_t(L->npartials)) : 0;  // one byte per CTA: its patch holds a solid site
   L->scal = take(64 * sizeof(double));
   L->staging_bytes = std::min<size_t>(kStagingMax, size_t(11) * 8 * size_t(N));
   L->staging = take(L->staging_bytes);
@@ -210,8 +209,6 @@ struct lbf_ctx {
   bool aligned;         // the forward kernel is the line-aligned one (TMA loads and stores)
   CUtensorMap tmap[2];  // tensor maps of the two state buffers (TMA source)
   CUtensorMap smap[2];  // tensor maps of the two state buffers (TMA store destination)
-  uint8_t* walls_d;     // per-CTA flag of the row-synchronised kernel: a solid site in its patch
-  std::vector<uint8_t> walls_h;
   bool sums_valid;
   bool unstable_seen;
   double omega, nu_l, nu_h;
@@ -515,8 +512,7 @@ lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
       if (st != LBF_OK) return st;
     }
   }
-  const uint8_t* walls = c->walls_d;
-  void* args[] = {&a, &tm, k->row_boxes ? static_cast<void*>(&walls) : static_cast<void*>(&sm)};
+  void* args[] = {&a, &tm, &sm};
   const dim3 grid(grid_x(c->nx, k->xout), grid_y(c->ny, k->by), c->fgrid.z);
   LBF_CUDA(cudaLaunchKernel(k->fn, grid, dim3(32, k->threads / 32, 1), args, k->smem, c->stream));
   return LBF_OK;
@@ -689,19 +685,22 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   c->fwd = forward_for(c->Q, c->storage, c->has_mask, two_mode, params->force_field != nullptr, c->tma, nearest);
   c->fwd_tma30 = c->fwd;
   c->aligned = false;
-  // single-component TMA steps: the row-synchronised kernel, or (LBF_KERNEL=aligned / cta) the
-  // line-aligned kernel or the CTA-synchronised one
+  // single-component TMA steps: the line-aligned kernel where it measured faster than the 30-column
+  // one on one GB300 (periodic D3Q19 in FP32 and 16-bit storage, periodic D3Q27 in FP32, planes of at
+  // least 512 x 512 sites: +11% D3Q19 FP32, +3% D3Q19 FP16, +2% D3Q27 FP32 at 512^3; slower with
+  // walls, on smaller planes, for D3Q27h and for 16-bit D3Q27). LBF_KERNEL=aligned or cta forces
+  // one of them.
   const char* kind = std::getenv("LBF_KERNEL");
-  const std::string kname = kind ? kind : "rows";
-  if (c->tma && !c->two && !c->pops && kname == "aligned") {
+  const std::string kname = kind ? kind : "";
+  const bool large = (long long)c->nx * c->ny >= 512LL * 512LL;
+  const bool policy = !c->has_mask && params->force_field == nullptr && large &&
+                      ((c->Q == LBF_D3Q19 && c->storage != LBF_F64) || (c->Q == LBF_D3Q27 && c->storage == LBF_F32));
+  if (c->tma && !c->two && !c->pops && (kname == "aligned" || (kname.empty() && policy))) {
     const KernelInfo al = aligned_kernel_for(c->Q, c->storage, c->has_mask, params->force_field != nullptr, nearest);
     if (al.fn != nullptr) {
       c->fwd = al;
       c->aligned = true;
     }
-  } else if (c->tma && !c->two && !c->pops && kname == "rows") {
-    const KernelInfo rk = rows_kernel_for(c->Q, c->storage, c->has_mask, params->force_field != nullptr, nearest);
-    if (rk.fn != nullptr) c->fwd = rk;
   }
   c->popk = c->pops ? pop_kernels_for(c->Q, c->storage, c->has_mask, params->force_field != nullptr)
                     : PopKernels{nullptr, nullptr, nullptr};
@@ -778,30 +777,6 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   if (c->has_mask) {
     if (cudaMemcpyAsync(c->mask_d, params->mask, c->N, cudaMemcpyHostToDevice, s) != cudaSuccess)
       return cleanup(fail(LBF_ECUDA, "mask copy failed"));
-    // per-CTA walls table of the row-synchronised kernel: does the patch it reads (planes
-    // z0 - 1 .. z1, rows y0 - 1 .. y0 + by, columns x0 - 1 .. x0 + 30, periodic) hold a solid site
-    if (c->fwd.row_boxes) {
-      c->walls_d = reinterpret_cast<uint8_t*>(c->ws + L.walls);
-      c->walls_h.assign(size_t(forward_blocks(c)), 0);
-      const int by = c->fwd.by, xo = c->fwd.xout;
-      const uint8_t* m = params->mask;
-      for (unsigned bz = 0; bz < c->fgrid.z; ++bz)
-        for (unsigned byi = 0; byi < c->fgrid.y; ++byi)
-          for (unsigned bx = 0; bx < c->fgrid.x; ++bx) {
-            const int z0 = int(bz) * c->zchunk, z1 = std::min(c->nz, z0 + c->zchunk);
-            bool any = false;
-            for (int z = z0 - 1; z <= z1 && !any; ++z)
-              for (int y = int(byi) * by - 1; y <= int(byi) * by + by && !any; ++y)
-                for (int x = int(bx) * xo - 1; x <= int(bx) * xo + xo && !any; ++x) {
-                  const int zz = (z % c->nz + c->nz) % c->nz, yy = (y % c->ny + c->ny) % c->ny,
-                            xx = (x % c->nx + c->nx) % c->nx;
-                  any = m[((long long)zz * c->ny + yy) * c->nx + xx] != 0;
-                }
-            c->walls_h[(size_t(bz) * c->fgrid.y + byi) * c->fgrid.x + bx] = any ? 1 : 0;
-          }
-      if (cudaMemcpyAsync(c->walls_d, c->walls_h.data(), c->walls_h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return cleanup(fail(LBF_ECUDA, "walls table copy failed"));
-    }
   }
   if (c->two) {
     const size_t cb = compute_bytes(c->storage);
@@ -1008,18 +983,30 @@ lbf_status lbf_debug_wait_probe(lbf_ctx* c, unsigned polls) {
 
 lbf_status lbf_synchronize(lbf_ctx* c) {
   if (c == nullptr) return fail(LBF_EINVAL, "NULL context");
-  unsigned f = 0;
-  LBF_CUDA(cudaMemcpyAsync(&f, c->flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
+  // flags[0]: error bits; flags[1], flags[2]: where the first bounded wait gave up (if recorded)
+  unsigned f3[4] = {0u, 0u, 0u, 0u};
+  LBF_CUDA(cudaMemcpyAsync(f3, c->flags, sizeof(f3), cudaMemcpyDeviceToHost, c->stream));
   LBF_CUDA(cudaStreamSynchronize(c->stream));
+  const unsigned f = f3[0];
+  const unsigned where[2] = {f3[1], f3[2]};
   // the error bits are reported once: clear them so that the context stays usable
   if (f & 14u) {
-    const unsigned keep = f & 1u;
-    LBF_CUDA(cudaMemcpyAsync(c->flags, &keep, sizeof(keep), cudaMemcpyHostToDevice, c->stream));
+    const unsigned keep[4] = {f & 1u, 0u, 0u, 0u};
+    LBF_CUDA(cudaMemcpyAsync(c->flags, keep, sizeof(keep), cudaMemcpyHostToDevice, c->stream));
     LBF_CUDA(cudaStreamSynchronize(c->stream));
   }
   if (f & 8u) return fail(LBF_EINTERNAL, "an index check of the LBF_DEBUG build failed");
-  if (f & 6u) return fail(LBF_EINTERNAL, (f & 4u) ? "a TMA stage was misaligned; the step was abandoned"
-                                                  : "a TMA plane load did not complete in time; the step was abandoned");
+  if (f & 6u) {
+    std::string msg = (f & 4u) ? "a TMA stage was misaligned; the step was abandoned"
+                               : "a bounded wait of the step did not complete in time; the step was abandoned";
+    if (where[0] & 0x80000000u) {
+      static const char* kinds[4] = {"?", "TMA stage", "neighbour row's populations", "freed ring slots"};
+      msg += std::string(" (first: ") + kinds[(where[0] >> 24) & 3u] + ", row " + std::to_string((where[0] >> 16) & 0xffu) +
+             ", plane " + std::to_string(int(where[0] & 0xffffu)) + " of the chunk, CTA " + std::to_string(where[1]) +
+             "; " + std::to_string(f3[3]) + " waits gave up)";
+    }
+    return fail(LBF_EINTERNAL, msg);
+  }
   if (f & 1u) c->unstable_seen = true;
   return c->unstable_seen ? fail(LBF_EUNSTABLE, "non-finite value or |u| > 0.4 in a step") : LBF_OK;
 }

@@ -7,7 +7,6 @@
 #include "population.cuh"
 #include "stream_collide.cuh"
 #include "stream_collide_aligned.cuh"
-#include "stream_collide_rows.cuh"
 
 namespace lbf {
 
@@ -25,7 +24,6 @@ struct KernelInfo {
   int box_x;        // TMA box width in elements (0: the kernel loads without TMA)
   int xout = 30;    // output columns per CTA: 30 (k_stream_collide) or 32 (k_stream_collide_al)
   bool store_map = false;  // the kernel also takes a tensor map of dst (TMA stores)
-  bool row_boxes = false;  // k_stream_collide_rows: takes a per-CTA walls table after the tensor map
 };
 
 template <class L, class S, bool MASK, int TWO, bool FF, bool TMA, bool RN>
@@ -126,34 +124,6 @@ KernelInfo aligned_kernel_ls(bool mask, bool field, bool nearest) {
   }
 }
 
-// row-synchronised kernel (single component, TMA loads)
-template <class L, class S, bool MASK, bool FF, bool RN>
-KernelInfo rows_info() {
-  constexpr int BY = fwd_rows_lattice(L::Q, int(sizeof(S)), MASK, false, L::HIGH);
-  KernelInfo k;
-  k.fn = reinterpret_cast<const void*>(&k_stream_collide_rows<L, S, BY, MASK, FF, RN>);
-  k.smem = rows_smem_bytes<L, S, BY, MASK>();
-  k.threads = FwdTile<BY>::THREADS;
-  k.by = BY;
-  k.box_x = TmaBox<S>::BX;
-  k.row_boxes = true;  // takes the per-CTA walls table (its tensor map is the 30-column kernel's)
-  return k;
-}
-
-template <class L, class S>
-KernelInfo rows_kernel_ls(bool mask, bool field, bool nearest) {
-  auto pick = [&](auto rn) {
-    constexpr bool RN = decltype(rn)::value;
-    if (mask) return field ? rows_info<L, S, true, true, RN>() : rows_info<L, S, true, false, RN>();
-    return field ? rows_info<L, S, false, true, RN>() : rows_info<L, S, false, false, RN>();
-  };
-  if constexpr (Codec<S>::scaled) {
-    if (nearest) return pick(std::true_type{});
-  }
-  (void)nearest;
-  return pick(std::false_type{});
-}
-
 // population-form reference kernels of lattice L, storage S (FP32/FP64 only; nulls otherwise)
 struct PopKernels {
   const void* step;     // k_pop_step
@@ -184,7 +154,6 @@ PopKernels pop_kernels_ls(bool mask, bool field) {
 #define LBF_DECLARE_TU(q, s)                                                             \
   KernelInfo forward_kernel_q##q##_s##s(bool mask, int two, bool field, bool tma, bool nearest); \
   KernelInfo aligned_kernel_q##q##_s##s(bool mask, bool field, bool nearest);                    \
-  KernelInfo rows_kernel_q##q##_s##s(bool mask, bool field, bool nearest);                       \
   PopKernels pop_kernels_q##q##_s##s(bool mask, bool field);                                        \
   KernelInfo adjoint_kernel_q##q##_s##s(bool mask);
 LBF_DECLARE_TU(19, 0)
@@ -244,26 +213,6 @@ inline KernelInfo aligned_kernel_for(int lattice, int storage, bool mask, bool f
     LBF_AL_CASE(127)
   }
 #undef LBF_AL_CASE
-  return KernelInfo{nullptr, 0, 0, 0, 0};
-}
-
-// row-synchronised kernel (every lattice and storage, single component)
-inline KernelInfo rows_kernel_for(int lattice, int storage, bool mask, bool field, bool nearest) {
-#define LBF_RW_CASE(q)                                                  \
-  switch (storage) {                                                   \
-    case ST_F64: return rows_kernel_q##q##_s0(mask, field, nearest);   \
-    case ST_F32: return rows_kernel_q##q##_s1(mask, field, nearest);   \
-    case ST_F16: return rows_kernel_q##q##_s2(mask, field, nearest);   \
-    case ST_BF16: return rows_kernel_q##q##_s3(mask, field, nearest);  \
-  }
-  if (lattice == 19) {
-    LBF_RW_CASE(19)
-  } else if (lattice == 27) {
-    LBF_RW_CASE(27)
-  } else if (lattice == 127) {
-    LBF_RW_CASE(127)
-  }
-#undef LBF_RW_CASE
   return KernelInfo{nullptr, 0, 0, 0, 0};
 }
 

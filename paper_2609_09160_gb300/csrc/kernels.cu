@@ -44,10 +44,6 @@ KernelInfo LBF_CAT(aligned_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool ma
   return aligned_kernel_ls<TuL, TuS>(mask, field, nearest);
 }
 
-KernelInfo LBF_CAT(rows_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask, bool field, bool nearest) {
-  return rows_kernel_ls<TuL, TuS>(mask, field, nearest);
-}
-
 PopKernels LBF_CAT(pop_kernels_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask, bool field) {
 #if LBF_TU_LATTICE == 127
   (void)mask;

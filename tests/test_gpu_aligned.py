@@ -1,5 +1,5 @@
 """The line-aligned fused kernel (32-column tiles, TMA tensor stores; FP32 and 16-bit storage, single
-component) against the 30-column kernel (LBF_NO_ALIGNED selects it at lbf_create) and against the
+component) against the 30-column kernel (LBF_KERNEL=aligned / cta select them at lbf_create) and against the
 oracle, on shapes that exercise partial tiles in x and y, the periodic wrap of the halo rows and
 columns, walls and force fields. Both kernels evaluate the same expressions in the same order; the
 compiler contracts a few of them into FMAs differently, so the states agree to a few units in the
@@ -20,15 +20,14 @@ LAT = {19: oracle.D3Q19, 27: oracle.D3Q27}
 
 
 def _solver(no_aligned, **kw):
-    old = os.environ.pop("LBF_NO_ALIGNED", None)
+    old = os.environ.pop("LBF_KERNEL", None)
     try:
-        if no_aligned:
-            os.environ["LBF_NO_ALIGNED"] = "1"
+        os.environ["LBF_KERNEL"] = "cta" if no_aligned else "aligned"
         return Solver(**kw)
     finally:
-        os.environ.pop("LBF_NO_ALIGNED", None)
+        os.environ.pop("LBF_KERNEL", None)
         if old is not None:
-            os.environ["LBF_NO_ALIGNED"] = old
+            os.environ["LBF_KERNEL"] = old
 
 
 SHAPES = [(5, 13, 64), (7, 9, 40), (3, 17, 96), (9, 6, 32)]
