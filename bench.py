@@ -58,7 +58,7 @@ def measured_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha1()
-    for name in ("lattice.cuh", "stream_collide.cuh"):
+    for name in ("lattice.cuh", "stream_collide.cuh", "stream_collide_aligned.cuh", "tma.cuh"):
         with open(os.path.join(ROOT, "paper_2609_09160_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]

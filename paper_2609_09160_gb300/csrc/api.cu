@@ -841,6 +841,13 @@ lbf_status lbf_set_moments(lbf_ctx* c, const void* src, int dt, const void* phi)
     if (dt == LBF_F64) encode_dispatch<double>(c->storage, src, N, 0, N, enc_dst, N, c->sc, s);
     else encode_dispatch<float>(c->storage, src, N, 0, N, enc_dst, N, c->sc, s);
     LBF_CUDA(cudaGetLastError());
+  } else if (!c->pops && storage_bytes(c->storage) >= eb) {
+    // the second state buffer holds the whole public state: one host copy (at the full host-link
+    // rate from pinned memory), then one encode pass on the device
+    LBF_CUDA(cudaMemcpyAsync(c->state[1], src, size_t(10) * N * eb, cudaMemcpyHostToDevice, s));
+    if (dt == LBF_F64) encode_dispatch<double>(c->storage, c->state[1], N, 0, N, enc_dst, N, c->sc, s);
+    else encode_dispatch<float>(c->storage, c->state[1], N, 0, N, enc_dst, N, c->sc, s);
+    LBF_CUDA(cudaGetLastError());
   } else {
     const long long chunk = std::max<long long>(1, (long long)(c->lay.staging_bytes / (10 * eb)));
     const unsigned char* h = static_cast<const unsigned char*>(src);
@@ -940,6 +947,16 @@ lbf_status lbf_moments(lbf_ctx* c, void* dst, int dt, void* phi_dst) {
     if (dt == LBF_F64) decode_dispatch<double>(c->storage, st, N, 0, N, dst, N, c->sc, s);
     else decode_dispatch<float>(c->storage, st, N, 0, N, dst, N, c->sc, s);
     LBF_CUDA(cudaGetLastError());
+  } else if (!c->pops && storage_bytes(c->storage) >= eb) {
+    // decode into the idle state buffer (the next step overwrites it anyway), then one host copy
+    void* scratch = c->state[1 - c->cur];
+    if (dt == LBF_F64) decode_dispatch<double>(c->storage, st, N, 0, N, scratch, N, c->sc, s);
+    else decode_dispatch<float>(c->storage, st, N, 0, N, scratch, N, c->sc, s);
+    LBF_CUDA(cudaGetLastError());
+    LBF_CUDA(cudaMemcpyAsync(dst, scratch, size_t(10) * N * eb, cudaMemcpyDeviceToHost, s));
+    // a step does not write solid sites: the idle buffer must keep their moments
+    if (c->has_mask)
+      LBF_CUDA(cudaMemcpyAsync(scratch, st, lbf_state_bytes(c), cudaMemcpyDeviceToDevice, s));
   } else {
     const long long chunk = std::max<long long>(1, (long long)(c->lay.staging_bytes / (10 * eb)));
     unsigned char* h = static_cast<unsigned char*>(dst);

@@ -1,6 +1,7 @@
 """Runs every forward-kernel variant on odd lattice shapes through the library named by
 LBF_LIBRARY (the index-checked LBF_DEBUG build in tests/test_gpu_index_checks.py) and prints one
 line per case with the status of lbf_synchronize; exits non-zero if any case fails."""
+import os
 import sys
 
 import torch
@@ -18,10 +19,17 @@ def cases():
                 if kind == "two" and storage in ("f16", "bf16"):
                     continue
                 for shape in SHAPES:
-                    yield lattice, storage, kind, shape
+                    yield lattice, storage, kind, shape, "cta"
+    # the line-aligned kernel (single component, FP32 and 16-bit storage) on the same shapes
+    for lattice in (19, 27):
+        for storage in ("f32", "f16", "bf16"):
+            for kind in ("periodic", "walls", "field"):
+                for shape in SHAPES:
+                    yield lattice, storage, kind, shape, "aligned"
 
 
-def run(lattice, storage, kind, shape):
+def run(lattice, storage, kind, shape, kernel):
+    os.environ["LBF_KERNEL"] = kernel
     cdt = torch.float64 if storage == "f64" else torch.float32
     kw = {}
     if kind == "walls":
