@@ -107,22 +107,12 @@ struct Codec<double> {
   __device__ __forceinline__ static void store(double* p, double v) { *p = v; }
   __device__ __forceinline__ static void store_sr(double* p, double v, uint32_t) { *p = v; }
 };
-// LBF_STORE_CS: the step's FP32 stores carry the streaming (evict-first) cache hint
-#ifndef LBF_STORE_CS
-#define LBF_STORE_CS 0
-#endif
 template <>
 struct Codec<float> {
   static constexpr bool scaled = false;
   __device__ __forceinline__ static float load(const float* p) { return __ldg(p); }
-  __device__ __forceinline__ static void store(float* p, float v) {
-#if LBF_STORE_CS
-    __stcs(p, v);
-#else
-    *p = v;
-#endif
-  }
-  __device__ __forceinline__ static void store_sr(float* p, float v, uint32_t) { store(p, v); }
+  __device__ __forceinline__ static void store(float* p, float v) { *p = v; }
+  __device__ __forceinline__ static void store_sr(float* p, float v, uint32_t) { *p = v; }
 };
 template <>
 struct Codec<__half> {

@@ -344,10 +344,6 @@ __device__ __forceinline__ void accumulate_couple(Accum2& A, float2 g, float2 o)
 #ifndef LBF_PACKED_ACC
 #define LBF_PACKED_ACC 1
 #endif
-// D3Q19 y-halo rows stage only the 5 directions pulled into the tile (1) or every direction (0)
-#ifndef LBF_HALO_DIRS_Q19
-#define LBF_HALO_DIRS_Q19 0
-#endif
 
 template <int BY>
 struct FwdTile {
@@ -806,7 +802,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
   // the reduced halo staging pays on D3Q27 (9 of 26 directions per halo row); on D3Q19 (5 of 18)
   // the extra code measured slower than staging every direction
   auto stage_row = [&](auto par_c, int p, int g2, const SiteExtra<T, TWO>& e) -> bool {
-    if constexpr ((L::Q == 27 && !L::HIGH) || (L::Q == 19 && LBF_HALO_DIRS_Q19)) {  // D3Q27h: one staging body
+    if constexpr (L::Q == 27 && !L::HIGH) {  // D3Q27h: one staging body (compile time)
       if (row == 0) return stage(par_c, std::integral_constant<int, 1>{}, p, g2, e);
       if (row == ROWS - 1) return stage(par_c, std::integral_constant<int, -1>{}, p, g2, e);
     }
