@@ -269,6 +269,17 @@ bool is_device_pointer(const void* p) {
   return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+// device address of page-locked host memory (mapped into the device's address space), or null for
+// pageable host memory: kernels read and write pinned buffers directly over the host link
+const void* mapped_host_pointer(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return attr.type == cudaMemoryTypeHost ? attr.devicePointer : nullptr;
+}
+
 unsigned blocks_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   return (unsigned)std::max<long long>(1, std::min<long long>(b, 65535LL * 16));
@@ -814,12 +825,14 @@ lbf_status lbf_set_moments(lbf_ctx* c, const void* src, int dt, const void* phi)
   cudaStream_t s = c->stream;
   if (c->storage == LBF_F16 || c->storage == LBF_BF16) {
     double m[3] = {0, 0, 0};
-    if (dev) {
+    // device memory, or pinned host memory read in place by the device
+    const void* src_dev = dev ? src : mapped_host_pointer(src);
+    if (src_dev != nullptr) {
       LBF_CUDA(cudaMemsetAsync(c->absmax, 0, 3 * sizeof(unsigned), s));
       if (dt == LBF_F64)
-        k_absmax<double><<<blocks_for(N, 256), 256, 0, s>>>(static_cast<const double*>(src), N, N, c->absmax);
+        k_absmax<double><<<blocks_for(N, 256), 256, 0, s>>>(static_cast<const double*>(src_dev), N, N, c->absmax);
       else
-        k_absmax<float><<<blocks_for(N, 256), 256, 0, s>>>(static_cast<const float*>(src), N, N, c->absmax);
+        k_absmax<float><<<blocks_for(N, 256), 256, 0, s>>>(static_cast<const float*>(src_dev), N, N, c->absmax);
       LBF_CUDA(cudaGetLastError());
       unsigned h[3];
       LBF_CUDA(cudaMemcpyAsync(h, c->absmax, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -841,9 +854,13 @@ lbf_status lbf_set_moments(lbf_ctx* c, const void* src, int dt, const void* phi)
     if (dt == LBF_F64) encode_dispatch<double>(c->storage, src, N, 0, N, enc_dst, N, c->sc, s);
     else encode_dispatch<float>(c->storage, src, N, 0, N, enc_dst, N, c->sc, s);
     LBF_CUDA(cudaGetLastError());
+  } else if (const void* mapped = mapped_host_pointer(src)) {
+    // pinned host memory: the encode pass reads it in place over the host link (one pass)
+    if (dt == LBF_F64) encode_dispatch<double>(c->storage, mapped, N, 0, N, enc_dst, N, c->sc, s);
+    else encode_dispatch<float>(c->storage, mapped, N, 0, N, enc_dst, N, c->sc, s);
+    LBF_CUDA(cudaGetLastError());
   } else if (!c->pops && storage_bytes(c->storage) >= eb) {
-    // the second state buffer holds the whole public state: one host copy (at the full host-link
-    // rate from pinned memory), then one encode pass on the device
+    // the second state buffer holds the whole public state: one host copy, then one encode pass
     LBF_CUDA(cudaMemcpyAsync(c->state[1], src, size_t(10) * N * eb, cudaMemcpyHostToDevice, s));
     if (dt == LBF_F64) encode_dispatch<double>(c->storage, c->state[1], N, 0, N, enc_dst, N, c->sc, s);
     else encode_dispatch<float>(c->storage, c->state[1], N, 0, N, enc_dst, N, c->sc, s);
@@ -946,6 +963,11 @@ lbf_status lbf_moments(lbf_ctx* c, void* dst, int dt, void* phi_dst) {
   if (is_device_pointer(dst)) {
     if (dt == LBF_F64) decode_dispatch<double>(c->storage, st, N, 0, N, dst, N, c->sc, s);
     else decode_dispatch<float>(c->storage, st, N, 0, N, dst, N, c->sc, s);
+    LBF_CUDA(cudaGetLastError());
+  } else if (void* mapped = const_cast<void*>(mapped_host_pointer(dst))) {
+    // pinned host memory: the decode pass writes it in place over the host link (one pass)
+    if (dt == LBF_F64) decode_dispatch<double>(c->storage, st, N, 0, N, mapped, N, c->sc, s);
+    else decode_dispatch<float>(c->storage, st, N, 0, N, mapped, N, c->sc, s);
     LBF_CUDA(cudaGetLastError());
   } else if (!c->pops && storage_bytes(c->storage) >= eb) {
     // decode into the idle state buffer (the next step overwrites it anyway), then one host copy

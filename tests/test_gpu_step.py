@@ -152,6 +152,36 @@ def test_host_buffers_round_trip_and_match_device_path():
     assert torch.equal(a.moments(dtype=torch.float32).cpu(), host)
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("walls", [False, True])
+def test_host_transfer_paths_agree(storage, walls):
+    """Every way a public state crosses the host link gives the device path's result: pinned host
+    memory read and written in place by the encode / decode passes, pageable host memory through the
+    idle state buffer (one copy) or, for 16-bit storage, through the staging area in chunks. With
+    walls, reading a state back must leave the solid sites of the idle buffer intact."""
+    shape = (7, 12, 40)
+    M0 = synth.random_moments(shape, seed=31)
+    mask = synth.channel_walls(shape) if walls else None
+    dt = torch.float64 if storage == "f64" else torch.float32
+    ref = Solver(shape, lattice=19, tau=0.7, storage=storage, force=(1e-5, 0.0, 0.0), mask=mask)
+    ref.set_moments(M0.to(dt).cuda())
+    ref.step(2)
+    want = ref.moments(dtype=dt).cpu()
+    for pinned_in in (True, False):
+        for pinned_out in (True, False):
+            s = Solver(shape, lattice=19, tau=0.7, storage=storage, force=(1e-5, 0.0, 0.0), mask=mask)
+            src = M0.to(dt)
+            s.set_moments(src.pin_memory() if pinned_in else src)
+            s.step(1)
+            mid = torch.empty((10,) + shape, dtype=dt).pin_memory() if pinned_out else torch.empty((10,) + shape, dtype=dt)
+            s.moments(dtype=dt, out=mid)  # read-back between steps must not disturb the next step
+            s.step(1)
+            out = torch.empty((10,) + shape, dtype=dt).pin_memory() if pinned_out else torch.empty((10,) + shape, dtype=dt)
+            got = s.moments(dtype=dt, out=out)
+            torch.cuda.synchronize()
+            assert torch.equal(got, want), (pinned_in, pinned_out)
+
+
 def test_instability_is_reported():
     shape = (4, 4, 32)
     M0 = synth.random_moments(shape, seed=2)
