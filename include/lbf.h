@@ -222,8 +222,8 @@ lbf_status lbf_adjoint_step(lbf_ctx* ctx, const void* state_t, const void* state
    for 16384 CTAs: ceil(nx/30) * ceil(ny/R) must not exceed 16384, else LBF_EINVAL, where R is the
    number of output rows per CTA of the kernel the parameters select (FP32: 8 for D3Q19 and for
    D3Q27/D3Q27H with a mask, 6 for D3Q27/D3Q27H without one; FP64: 4); the error message names R.
-   The first call on a device looks up that array's device address; make it before any stream
-   capture. Every call clears the counter and flags it needs (cudaMemsetAsync, which does not
+   The first call on a device looks up that array's device address (cudaGetSymbolAddress) and
+   keeps it for later calls. Every call clears the counter and flags it needs (cudaMemsetAsync, which does not
    allocate). All calls share the array: calls that can overlap on the GPU (other streams, other
    host threads) race on it; calls ordered on one stream are safe. Asynchronous on params->stream.
    Paper: no counterpart; it runs the step of Eq. (pullLLB) + Eq. (corr), Sec. 2. */
