@@ -122,13 +122,6 @@ int aligned_by(const lbf_params* p) {
   return al_rows(p->lattice == LBF_D3Q19 ? 19 : 27, int(storage_bytes(p->storage)), p->mask != nullptr,
                  p->lattice == LBF_D3Q27H);
 }
-// output rows of the two-sites-per-thread kernel for these parameters (0 when it is not built for them)
-int pair_by(const lbf_params* p) {
-  if (p->two_component || p->populations || p->storage != LBF_F32 || p->force_field != nullptr ||
-      (p->lattice != LBF_D3Q19 && p->lattice != LBF_D3Q27))
-    return 0;
-  return p2_rows(p->lattice);
-}
 
 bool make_layout(const lbf_params* p, Layout* L) {
   if (check_params(p) != LBF_OK) return false;
@@ -161,7 +154,6 @@ bool make_layout(const lbf_params* p, Layout* L) {
   // per-block partial sums of the largest grid either forward kernel can launch
   long long tiles = (long long)grid_x(p->nx) * grid_y(p->ny, fwd_by(p->lattice, p->storage, p->mask != nullptr, p->two_component != 0));
   if (const int aby = aligned_by(p)) tiles = std::max(tiles, (long long)grid_x(p->nx, 32) * grid_y(p->ny, aby));
-  if (const int pby = pair_by(p)) tiles = std::max(tiles, (long long)grid_x(p->nx) * grid_y(p->ny, pby));
   L->npartials = std::max<long long>(tiles * gz, 1024);
   L->partials = take(size_t(L->npartials) * 8 * sizeof(double));
   L->scal = take(64 * sizeof(double));
@@ -719,15 +711,6 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
     if (al.fn != nullptr) {
       c->fwd = al;
       c->aligned = true;
-    }
-  }
-  // two sites per thread with packed FP32 arithmetic (FP32 storage, uniform force)
-  const bool pair_policy = false;
-  if (c->tma && !c->aligned && pair_by(params) != 0 && (kname == "pair" || (kname.empty() && pair_policy))) {
-    const KernelInfo pk = pair_kernel_for(c->Q, c->storage, c->has_mask);
-    if (pk.fn != nullptr) {
-      c->fwd = pk;
-      c->fwd_tma30 = pk;
     }
   }
   c->popk = c->pops ? pop_kernels_for(c->Q, c->storage, c->has_mask, params->force_field != nullptr)

@@ -7,7 +7,6 @@
 #include "population.cuh"
 #include "stream_collide.cuh"
 #include "stream_collide_aligned.cuh"
-#include "stream_collide_pair.cuh"
 
 namespace lbf {
 
@@ -125,29 +124,6 @@ KernelInfo aligned_kernel_ls(bool mask, bool field, bool nearest) {
   }
 }
 
-// two-sites-per-thread kernel (FP32 storage, D3Q19 / D3Q27, single component, uniform force)
-template <class L, bool MASK>
-KernelInfo p2_info() {
-  constexpr int BY = p2_rows(L::Q);
-  KernelInfo k;
-  k.fn = reinterpret_cast<const void*>(&k_stream_collide_p2<L, BY, MASK>);
-  k.smem = p2_smem_bytes<L, BY, MASK>();
-  k.threads = P2Tile<BY>::THREADS;
-  k.by = BY;
-  k.box_x = TmaBox<float>::BX;
-  return k;
-}
-
-template <class L, class S>
-KernelInfo pair_kernel_ls(bool mask) {
-  if constexpr (std::is_same<S, float>::value && !L::HIGH) {
-    return mask ? p2_info<L, true>() : p2_info<L, false>();
-  } else {
-    (void)mask;
-    return KernelInfo{nullptr, 0, 0, 0, 0};
-  }
-}
-
 // population-form reference kernels of lattice L, storage S (FP32/FP64 only; nulls otherwise)
 struct PopKernels {
   const void* step;     // k_pop_step
@@ -178,7 +154,6 @@ PopKernels pop_kernels_ls(bool mask, bool field) {
 #define LBF_DECLARE_TU(q, s)                                                             \
   KernelInfo forward_kernel_q##q##_s##s(bool mask, int two, bool field, bool tma, bool nearest); \
   KernelInfo aligned_kernel_q##q##_s##s(bool mask, bool field, bool nearest);                    \
-  KernelInfo pair_kernel_q##q##_s##s(bool mask);                                                  \
   PopKernels pop_kernels_q##q##_s##s(bool mask, bool field);                                        \
   KernelInfo adjoint_kernel_q##q##_s##s(bool mask);
 LBF_DECLARE_TU(19, 0)
@@ -238,14 +213,6 @@ inline KernelInfo aligned_kernel_for(int lattice, int storage, bool mask, bool f
     LBF_AL_CASE(127)
   }
 #undef LBF_AL_CASE
-  return KernelInfo{nullptr, 0, 0, 0, 0};
-}
-
-// two-sites-per-thread kernel; fn == nullptr where it is not built (storage other than FP32, D3Q27h)
-inline KernelInfo pair_kernel_for(int lattice, int storage, bool mask) {
-  if (storage != ST_F32) return KernelInfo{nullptr, 0, 0, 0, 0};
-  if (lattice == 19) return pair_kernel_q19_s1(mask);
-  if (lattice == 27) return pair_kernel_q27_s1(mask);
   return KernelInfo{nullptr, 0, 0, 0, 0};
 }
 

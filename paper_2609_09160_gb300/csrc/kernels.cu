@@ -1,6 +1,6 @@
 // Kernel instantiations of one (lattice, storage) pair: the fused step in every force / mask / TMA
-// variant (30-column tiles, line-aligned 32-column tiles with TMA stores for FP32 and 16-bit
-// storage, two sites per thread for FP32 storage) and, for FP64 and FP32 storage, its adjoint. The build compiles this file once per pair
+// variant (30-column tiles, and line-aligned 32-column tiles with TMA stores for FP32 and 16-bit
+// storage) and, for FP64 and FP32 storage, its adjoint. The build compiles this file once per pair
 // with LBF_TU_LATTICE (19, 27 or 127 = D3Q27h) and LBF_TU_STORAGE (0 FP64, 1 FP32, 2 FP16, 3 BF16) defined.
 #include "dispatch.cuh"
 
@@ -42,10 +42,6 @@ KernelInfo LBF_CAT(forward_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool ma
 
 KernelInfo LBF_CAT(aligned_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask, bool field, bool nearest) {
   return aligned_kernel_ls<TuL, TuS>(mask, field, nearest);
-}
-
-KernelInfo LBF_CAT(pair_kernel_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask) {
-  return pair_kernel_ls<TuL, TuS>(mask);
 }
 
 PopKernels LBF_CAT(pop_kernels_q, LBF_TU_LATTICE, _s, LBF_TU_STORAGE)(bool mask, bool field) {

@@ -26,11 +26,6 @@ def cases():
             for kind in ("periodic", "walls", "field"):
                 for shape in SHAPES:
                     yield lattice, storage, kind, shape, "aligned"
-    # the two-sites-per-thread kernel (FP32 storage, uniform force) on the same shapes
-    for lattice in (19, 27):
-        for kind in ("periodic", "walls"):
-            for shape in SHAPES:
-                yield lattice, "f32", kind, shape, "pair"
 
 
 def run(lattice, storage, kind, shape, kernel):
