@@ -162,6 +162,7 @@ WORKLOADS = {
     "tg512_d3q27h_f32": (127, "f32", "tg512"),
     "tg512_d3q27h_f16": (127, "f16", "tg512"),
     "droplet128": (19, "f32", "droplet"),
+    "layered512": (19, "f32", "layered"),
     "adjoint128": (19, "f32", "adjoint"),
 }
 
@@ -173,6 +174,10 @@ def workload_solver(torch, device, key):
         return channel_solver(torch, device, storage, lattice)
     if kind == "droplet":
         return droplet_solver(torch, device)
+    if kind == "layered":
+        s, M0, phi0 = layered_solver(torch, device)
+        s._phi0 = phi0
+        return s, M0, None
     import synth
     from paper_2609_09160_gb300 import Solver
 
@@ -546,7 +551,7 @@ def run_ours(args):
                               "higher_is_better": False, "workload": args.workload}), flush=True)
         return
     s, M0, solid = workload_solver(torch, device, args.workload)
-    if WORKLOADS[args.workload][2] == "droplet":
+    if WORKLOADS[args.workload][2] in ("droplet", "layered"):
         s.set_moments(M0, s._phi0)
     else:
         s.set_moments(M0.to(device))
@@ -568,14 +573,19 @@ def run_ours(args):
     bpl = algorithmic_bytes(storage, mask=(kind == "channel"))
     if kind == "droplet":
         bpl += TWO_COMPONENT_EXTRA_BYTES
+    if kind == "layered":
+        bpl = algorithmic_bytes(storage, mask=True) + TWO_COMPONENT_EXTRA_BYTES + CONTRAST_EXTRA_BYTES
     t_launch = t / args.steps
     achieved = bpl * n / t_launch / 1e9
     traffic = ncu_traffic(args.workload)
     desc = {"channel": WORKLOAD,
             "droplet": "two-component D3Q19 FP32 128^3 static droplet R=20, W=4, sigma=0.03, D=0.1, tau=1",
+            "layered": ("two-component D3Q19 FP32 layered flow with density contrast 512(x) x 1024(y) x 8(z): walls "
+                        "x=0,511, rho 0.5/1.5, nu 0.05/0.4, W=4, body acceleration 1e-7 along y"),
             "tg512": (f"{LATTICE_NAME[lattice]} {storage.upper()} storage, 512^3 periodic Taylor-Green U0=0.04 + random-phase "
                       "perturbation RMS 0.01 (seed 3), tau=0.55")}[kind]
-    shape_xyz = {"channel": [256, 256, 256], "droplet": [128, 128, 128], "tg512": [512, 512, 512]}[kind]
+    shape_xyz = {"channel": [256, 256, 256], "droplet": [128, 128, 128], "tg512": [512, 512, 512],
+                 "layered": [512, 1024, 8]}[kind]
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t * 1e3 / args.steps, 5), "higher_is_better": True,
@@ -585,9 +595,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": f"k_stream_collide<D3Q{lattice},{storage},{'mask' if kind == 'channel' else 'periodic'}>",
+                     "kernel": f"k_stream_collide<D3Q{lattice},{storage},{'mask' if kind in ('channel', 'layered') else 'periodic'}>",
                      "bytes_per_lup": bpl, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (3 if kind in ("droplet", "layered") else 1),
         "clocks": clocks,
         "sums_after": {"sum_p": sums[0], "sum_ux": sums[1]},
     }

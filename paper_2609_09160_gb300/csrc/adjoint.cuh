@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS)
   constexpr int REST = rest_index<L>();
   constexpr int PLANE = Q * ROWS * 32;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* nus = reinterpret_cast<T*>(smem_raw);
   uint8_t* msk = reinterpret_cast<uint8_t*>(smem_raw + size_t(3) * PLANE * sizeof(T));
 
