@@ -284,27 +284,42 @@ def time_steps(torch, s, steps, warmup, barrier=None):
 
 def e2e_measure(torch, device, steps):
     """Same metric through the public API with host buffers: upload the public state from pinned
-    host memory, run the steps reading the FP64 conservation sums back to the host after every step
-    (one 48-byte read each), download the final state to pinned host memory."""
+    host memory, run the steps copying the FP64 conservation sums of every step to pinned host
+    memory (one 48-byte device-to-host copy per step, Solver.reduce_async: no host wait between
+    steps), download the final state to pinned host memory; the host checks the last sums after
+    the final synchronisation. "blocking_reduce" is the same leg with Solver.reduce (the host waits
+    for every step's sums before launching the next step)."""
     s, M0, _ = channel_solver(torch, device)
     host_in = M0.pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
+    series = torch.empty((steps, 6), dtype=torch.float64).pin_memory()
     s.set_moments(host_in)
     s.step(3)
     s.reduce()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    s.set_moments(host_in)
-    for _ in range(steps):
-        s.step(1)
-        s.reduce()
-    s.moments(out=host_out)
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t0
     n = M0[0].numel()
     nbytes = host_in.numel() * host_in.element_size()
-    return {"value": n * steps / t / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nbytes / steps,
-            "d2h_bytes_per_step": 48 + nbytes / steps}
+
+    def leg(blocking):
+        t0 = time.perf_counter()
+        s.set_moments(host_in)
+        for k in range(steps):
+            s.step(1)
+            if blocking:
+                s.reduce()
+            else:
+                s.reduce_async(series[k])
+        s.moments(out=host_out)
+        s.synchronize()
+        t = time.perf_counter() - t0
+        if not blocking and not all(math.isfinite(v) for v in series[steps - 1].tolist()):
+            raise RuntimeError("non-finite sums in the end-to-end leg")
+        return n * steps / t / 1e6
+
+    value = leg(False)
+    blocking = leg(True)
+    return {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes / steps,
+            "d2h_bytes_per_step": 48 + nbytes / steps, "blocking_reduce": round(blocking, 2)}
 
 
 def _time_oracle_steps(step, target_seconds, max_steps):

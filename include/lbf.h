@@ -163,6 +163,16 @@ lbf_status lbf_moments(lbf_ctx* ctx, void* dst, int dst_dtype, void* phi_dst);
    totals that Eq. (pullLLB) conserves (sum p*, sum u without force, sum phi of Eq. ACeq). */
 lbf_status lbf_reduce(lbf_ctx* ctx, double* out);
 
+/* The sums of lbf_reduce without waiting: enqueues a copy of the 6 FP64 sums of the current state
+   into dst (6 doubles, DEVICE or pinned HOST memory) on the stream and returns. dst holds them once
+   the stream has passed the copy (after lbf_synchronize, or an event the caller records). A step
+   that follows overwrites the library's copy, not dst, so one dst per step collects a time series
+   without stalling the stream. Pageable host memory also works, but the copy then waits (CUDA's
+   rule for such copies). Errors of the steps (LBF_EUNSTABLE, LBF_EINTERNAL) are reported by the
+   next lbf_synchronize or lbf_reduce, not here.
+   Paper: as lbf_reduce (Sec. 4 energy diagnostic E(t); the totals Eq. (pullLLB) conserves). */
+lbf_status lbf_reduce_async(lbf_ctx* ctx, double* dst);
+
 /* Waits for the stream; LBF_EUNSTABLE as for lbf_reduce; LBF_EINTERNAL if a step was abandoned
    (a bounded TMA wait gave up, or an index check of the LBF_DEBUG build failed). Such an error is
    reported once and then cleared, so the context stays usable; the state it left is incomplete.

@@ -15,7 +15,7 @@ LBF_ROUND_STOCHASTIC, LBF_ROUND_NEAREST = 0, 1
 
 # every symbol declared in include/lbf.h
 EXPORTS = ("lbf_workspace_bytes", "lbf_validate", "lbf_create", "lbf_set_moments", "lbf_step", "lbf_moments",
-           "lbf_reduce", "lbf_synchronize", "lbf_state_bytes", "lbf_copy_state", "lbf_load_state",
+           "lbf_reduce", "lbf_reduce_async", "lbf_synchronize", "lbf_state_bytes", "lbf_copy_state", "lbf_load_state",
            "lbf_step_state", "lbf_adjoint_step", "lbf_step_static", "lbf_destroy", "lbf_status_string",
            "lbf_last_error", "lbf_version")
 
@@ -59,6 +59,7 @@ def load_library(path=LIB_PATH):
         "lbf_step": (I, [VP, I]),
         "lbf_moments": (I, [VP, VP, I, VP]),
         "lbf_reduce": (I, [VP, P(D)]),
+        "lbf_reduce_async": (I, [VP, VP]),
         "lbf_synchronize": (I, [VP]),
         "lbf_state_bytes": (SZ, [VP]),
         "lbf_copy_state": (I, [VP, VP]),
@@ -119,6 +120,10 @@ def lbf_reduce(ctx):
     out = (ctypes.c_double * 6)()
     _check(load_library().lbf_reduce(ctx, out))
     return [out[i] for i in range(6)]
+
+
+def lbf_reduce_async(ctx, dst_ptr):
+    _check(load_library().lbf_reduce_async(ctx, ctypes.c_void_p(dst_ptr)))
 
 
 def lbf_synchronize(ctx):

@@ -1063,6 +1063,16 @@ lbf_status lbf_reduce(lbf_ctx* c, double* out) {
   return st;
 }
 
+lbf_status lbf_reduce_async(lbf_ctx* c, double* dst) {
+  if (c == nullptr || dst == nullptr) return fail(LBF_EINVAL, "NULL argument");
+  if (!c->sums_valid) {
+    lbf_status st = reduce_state(c);
+    if (st != LBF_OK) return st;
+  }
+  LBF_CUDA(cudaMemcpyAsync(dst, c->sums, 6 * sizeof(double), cudaMemcpyDefault, c->stream));
+  return LBF_OK;
+}
+
 lbf_status lbf_copy_state(lbf_ctx* c, void* dst) {
   if (c == nullptr || dst == nullptr) return fail(LBF_EINVAL, "NULL argument");
   LBF_CUDA(cudaMemcpyAsync(dst, c->state[c->cur], lbf_state_bytes(c), cudaMemcpyDeviceToDevice, c->stream));

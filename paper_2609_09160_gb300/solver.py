@@ -136,6 +136,17 @@ class Solver:
         """[sum p*, sum ux, sum uy, sum uz, sum phi, sum u.u] over fluid sites (FP64)."""
         return _lbf.lbf_reduce(self.ctx)
 
+    def reduce_async(self, out=None):
+        """The sums of reduce() copied into `out` (6 float64: a CUDA tensor or pinned host memory,
+        default a new pinned host tensor) without waiting; valid once the stream has passed the
+        copy (after synchronize()). Step errors surface at the next synchronize() or reduce()."""
+        if out is None:
+            out = torch.empty(6, dtype=torch.float64).pin_memory()
+        if out.dtype != torch.float64 or out.numel() < 6 or not out.is_contiguous():
+            raise ValueError("reduce_async needs a contiguous float64 buffer of 6 values")
+        _lbf.lbf_reduce_async(self.ctx, out.data_ptr())
+        return out
+
     def synchronize(self):
         _lbf.lbf_synchronize(self.ctx)
 

@@ -123,6 +123,32 @@ def test_conservation_sums(storage):
     assert abs(r1[5] / 2 / n - ref1[5].item()) < 1e-5 * ref1[5].item()
 
 
+def test_reduce_async_matches_reduce():
+    """lbf_reduce_async copies, without waiting, the same FP64 sums lbf_reduce returns: one pinned
+    host row per step collects the series, and a device buffer gets the latest ones."""
+    shape = (6, 20, 32)
+    M0 = synth.random_moments(shape, seed=47)
+    kw = dict(lattice=19, tau=0.8, storage="f32", force=(1e-5, 0.0, 0.0), mask=synth.channel_walls(shape))
+    a = Solver(shape, **kw)
+    a.set_moments(M0.cuda())
+    series = torch.empty((4, 6), dtype=torch.float64).pin_memory()
+    dev = torch.full((6,), float("nan"), dtype=torch.float64, device="cuda")
+    for k in range(4):
+        a.step(1)
+        a.reduce_async(series[k])
+    a.reduce_async(dev)
+    a.synchronize()
+    b = Solver(shape, **kw)
+    b.set_moments(M0.cuda())
+    want = []
+    for k in range(4):
+        b.step(1)
+        want.append(b.reduce())
+    assert series.tolist() == want  # the step is bitwise deterministic
+    assert dev.cpu().tolist() == want[-1]
+    assert a.reduce() == want[-1]
+
+
 def test_fused_sums_match_standalone_reduction():
     shape = (9, 20, 45)
     M0, solid = synth.channel(shape, 1e-3, seed=4)
