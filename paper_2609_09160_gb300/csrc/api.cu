@@ -697,13 +697,15 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   c->fwd_tma30 = c->fwd;
   c->aligned = false;
   // single-component TMA steps: the line-aligned kernel where it measured faster than the 30-column
-  // one on one GB300 (periodic D3Q19 in FP32 and 16-bit storage, periodic D3Q27 in FP32, planes of at
-  // least 512 x 512 sites: +11% D3Q19 FP32, +3% D3Q19 FP16, +2% D3Q27 FP32 at 512^3; slower with
-  // walls, on smaller planes, for D3Q27h and for 16-bit D3Q27). LBF_KERNEL=aligned or cta forces
-  // one of them.
+  // one on one GB300: periodic D3Q19 FP32 on planes of at least 256 x 256 sites (8-row tiles: +23%
+  // at 512^3, +8% at 256^3), periodic D3Q19 16-bit and D3Q27 FP32 on planes of at least 512 x 512
+  // (+3%, +2% at 512^3); slower with walls, for D3Q27h and for 16-bit D3Q27. LBF_KERNEL=aligned or
+  // cta forces one of them.
   const char* kind = std::getenv("LBF_KERNEL");
   const std::string kname = kind ? kind : "";
-  const bool large = (long long)c->nx * c->ny >= 512LL * 512LL;
+  const long long plane_sites = (long long)c->nx * c->ny;
+  const bool q19_f32 = c->Q == LBF_D3Q19 && c->storage == LBF_F32;
+  const bool large = plane_sites >= (q19_f32 ? 256LL * 256LL : 512LL * 512LL);
   const bool policy = !c->has_mask && params->force_field == nullptr && large &&
                       ((c->Q == LBF_D3Q19 && c->storage != LBF_F64) || (c->Q == LBF_D3Q27 && c->storage == LBF_F32));
   if (c->tma && !c->two && !c->pops && (kname == "aligned" || (kname.empty() && policy))) {

@@ -93,9 +93,14 @@ constexpr size_t al_smem_bytes() {
 }
 
 // output rows per CTA and minimum resident CTAs of the aligned kernel, per lattice, storage width,
-// walls and basis (tuning defines LBF_AL_ROWS_*)
+// walls and basis (tuning defines LBF_AL_ROWS_*). D3Q19 FP32: 8 rows without walls (the tallest
+// tile at 3 CTAs/SM, 75.9 KB; 64.9 GLUPS at 512^3 against 58.4 for 6 rows and 60.5 / 60.9 for 5 / 7),
+// 7 rows with walls (the solid-flag ring and the second c_z = -1 slot need 3 KB more per CTA)
 #ifndef LBF_AL_ROWS_Q19
-#define LBF_AL_ROWS_Q19 6
+#define LBF_AL_ROWS_Q19 7
+#endif
+#ifndef LBF_AL_ROWS_Q19_NM
+#define LBF_AL_ROWS_Q19_NM 8
 #endif
 #ifndef LBF_AL_ROWS_Q19_16
 #define LBF_AL_ROWS_Q19_16 8
@@ -113,7 +118,7 @@ constexpr size_t al_smem_bytes() {
 #define LBF_AL_ROWS_Q27H_16 5
 #endif
 constexpr int al_rows(int Q, int bytes, bool mask, bool high) {
-  return Q == 19 ? (bytes == 4 ? LBF_AL_ROWS_Q19 : LBF_AL_ROWS_Q19_16)
+  return Q == 19 ? (bytes == 4 ? (mask ? LBF_AL_ROWS_Q19 : LBF_AL_ROWS_Q19_NM) : LBF_AL_ROWS_Q19_16)
                  : (bytes == 4 ? (mask ? LBF_AL_ROWS_Q27 : LBF_AL_ROWS_Q27_NM)
                                : (high ? LBF_AL_ROWS_Q27H_16 : LBF_AL_ROWS_Q27_16));
 }
