@@ -65,7 +65,8 @@ def kernel_source_sha():
 
 
 def ncu_traffic(workload_key):
-    """dram bytes per launch recorded from an ncu capture of the current kernel source, else None."""
+    """dram bytes of one step (all its launches) recorded from an ncu capture of the current kernel
+    source, else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -73,7 +74,7 @@ def ncu_traffic(workload_key):
     for line in open(path):
         parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if parts.get("workload") == workload_key and parts.get("kernel_sha") == sha:
-            return float(parts["bytes_per_launch"])
+            return float(parts.get("bytes_per_step", parts.get("bytes_per_launch")))
     return None
 
 
@@ -161,6 +162,12 @@ WORKLOADS = {
     "tg512_d3q19_f16": (19, "f16", "tg512"),
     "tg512_d3q27h_f32": (127, "f32", "tg512"),
     "tg512_d3q27h_f16": (127, "f16", "tg512"),
+    # 256^3 periodic Taylor-Green: the same kernels on a lattice small enough for ncu captures
+    "tg256_d3q19_f32": (19, "f32", "tg256"),
+    "tg256_d3q27_f32": (27, "f32", "tg256"),
+    "tg256_d3q27h_f32": (127, "f32", "tg256"),
+    "tg256_d3q19_f16": (19, "f16", "tg256"),
+    "tg256_d3q27_f16": (27, "f16", "tg256"),
     "droplet128": (19, "f32", "droplet"),
     "layered512": (19, "f32", "layered"),
     "adjoint128": (19, "f32", "adjoint"),
@@ -181,7 +188,7 @@ def workload_solver(torch, device, key):
     import synth
     from paper_2609_09160_gb300 import Solver
 
-    n = 512
+    n = 512 if kind == "tg512" else 256
     M0 = synth.taylor_green_perturbed(n, 0.04, 0.55, 0.01, seed=3, dtype=torch.float32, device=device)
     s = Solver((n, n, n), lattice=lattice, tau=0.55, storage=storage, device=device)
     return s, M0, None
@@ -263,7 +270,8 @@ def channel_solver(torch, device, storage="f32", lattice=19, shape=SHAPE, popula
 
 
 def time_steps(torch, s, steps, warmup, barrier=None):
-    """Device time of `steps` fused steps (one kernel each) on the solver's stream."""
+    """Device time of `steps` steps on the solver's stream (Solver.kernels_per_step launches each;
+    launches on the library's side stream are joined back to it before the step ends)."""
     for _ in range(warmup):
         s.step(1)
     torch.cuda.synchronize()
@@ -541,6 +549,19 @@ def replicas_mlups(world, sites_per_rank, steps, t):
     return world * sites_per_rank * steps / t / 1e6
 
 
+def kernel_label(s, lattice, storage, kind):
+    """The kernels one timed step runs (the roofline unit is one step: its launches together)."""
+    lat = LATTICE_NAME[lattice]
+    walls = kind in ("channel", "layered")
+    if s.kernels_per_step == 3 and walls and kind == "channel":
+        return (f"k_stream_collide_al<{lat},{storage},periodic> on the rows clear of the walls + "
+                f"k_stream_collide<{lat},{storage},mask> on the rows near them + k_reduce_final")
+    fused = f"k_stream_collide<{lat},{storage},{'mask' if walls else 'periodic'}>"
+    if kind in ("droplet", "layered"):
+        return f"k_phase_advance + k_phase_forces + {fused}"
+    return fused
+
+
 def run_ours(args):
     import torch
 
@@ -598,8 +619,10 @@ def run_ours(args):
             "layered": ("two-component D3Q19 FP32 layered flow with density contrast 512(x) x 1024(y) x 8(z): walls "
                         "x=0,511, rho 0.5/1.5, nu 0.05/0.4, W=4, body acceleration 1e-7 along y"),
             "tg512": (f"{LATTICE_NAME[lattice]} {storage.upper()} storage, 512^3 periodic Taylor-Green U0=0.04 + random-phase "
+                      "perturbation RMS 0.01 (seed 3), tau=0.55"),
+            "tg256": (f"{LATTICE_NAME[lattice]} {storage.upper()} storage, 256^3 periodic Taylor-Green U0=0.04 + random-phase "
                       "perturbation RMS 0.01 (seed 3), tau=0.55")}[kind]
-    shape_xyz = {"channel": [256, 256, 256], "droplet": [128, 128, 128], "tg512": [512, 512, 512],
+    shape_xyz = {"channel": [256, 256, 256], "droplet": [128, 128, 128], "tg512": [512, 512, 512], "tg256": [256, 256, 256],
                  "layered": [512, 1024, 8]}[kind]
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -610,9 +633,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": f"k_stream_collide<D3Q{lattice},{storage},{'mask' if kind in ('channel', 'layered') else 'periodic'}>",
+                     "kernel": kernel_label(s, lattice, storage, kind),
                      "bytes_per_lup": bpl, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
-        "gpu_launches": args.steps * (3 if kind in ("droplet", "layered") else 1),
+        "gpu_launches": args.steps * s.kernels_per_step,
         "clocks": clocks,
         "sums_after": {"sum_p": sums[0], "sum_ux": sums[1]},
     }

@@ -17,7 +17,7 @@ LBF_ROUND_STOCHASTIC, LBF_ROUND_NEAREST = 0, 1
 EXPORTS = ("lbf_workspace_bytes", "lbf_validate", "lbf_create", "lbf_set_moments", "lbf_step", "lbf_moments",
            "lbf_reduce", "lbf_reduce_async", "lbf_synchronize", "lbf_state_bytes", "lbf_copy_state", "lbf_load_state",
            "lbf_step_state", "lbf_adjoint_step", "lbf_step_static", "lbf_destroy", "lbf_status_string",
-           "lbf_last_error", "lbf_version")
+           "lbf_last_error", "lbf_version", "lbf_kernels_per_step")
 
 
 class lbf_params(ctypes.Structure):
@@ -71,6 +71,7 @@ def load_library(path=LIB_PATH):
         "lbf_status_string": (ctypes.c_char_p, [I]),
         "lbf_last_error": (ctypes.c_char_p, []),
         "lbf_version": (I, []),
+        "lbf_kernels_per_step": (I, [VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -185,3 +186,7 @@ def lbf_last_error():
 
 def lbf_version():
     return load_library().lbf_version()
+
+
+def lbf_kernels_per_step(ctx):
+    return load_library().lbf_kernels_per_step(ctx)

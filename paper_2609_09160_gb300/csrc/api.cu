@@ -154,7 +154,8 @@ bool make_layout(const lbf_params* p, Layout* L) {
   // per-block partial sums of the largest grid either forward kernel can launch
   long long tiles = (long long)grid_x(p->nx) * grid_y(p->ny, fwd_by(p->lattice, p->storage, p->mask != nullptr, p->two_component != 0));
   if (const int aby = aligned_by(p)) tiles = std::max(tiles, (long long)grid_x(p->nx, 32) * grid_y(p->ny, aby));
-  L->npartials = std::max<long long>(tiles * gz, 1024);
+  // walls: the step may be split into two launches over row ranges (clean rows, rows near walls)
+  L->npartials = std::max<long long>(tiles * gz * (p->mask != nullptr ? 2 : 1), 1024);
   L->partials = take(size_t(L->npartials) * 8 * sizeof(double));
   L->scal = take(64 * sizeof(double));
   L->staging_bytes = std::min<size_t>(kStagingMax, size_t(11) * 8 * size_t(N));
@@ -217,6 +218,17 @@ struct lbf_ctx {
   PopKernels popk;
   void* mom;                      // pops: internal moment state (read-out target, solid sites kept)
   dim3 pop_grid;                  // pops: (ceil(nx / 256), ny, nz) blocks of 256 threads
+  // walls confined to a band of rows: the rows clear of every solid site and of its neighbours
+  // ("clean") run the periodic line-aligned kernel, the others the masked 30-column kernel on a
+  // side stream; a one-block kernel then adds both launches' partial sums
+  bool split;
+  int clean_begin, clean_rows, dirty_begin, dirty_rows;
+  KernelInfo fwd_clean;
+  dim3 grid_clean, grid_dirty;
+  int zchunk_clean, zchunk_dirty;
+  CUtensorMap tmap_clean[2];
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
 };
 
 namespace {
@@ -479,6 +491,144 @@ lbf_status encode_state_map(const lbf_ctx* c, const void* base, CUtensorMap* out
   return LBF_OK;
 }
 
+// z-chunk of a launch of `tiles` x-y tiles: the CTAs of one tile column march through nz / chunks
+// planes each; the chunk count minimises (1 + restaged planes) / (fraction of the last wave busy)
+int choose_zchunk(int nz, long long tiles, double resident) {
+  int zc = nz;
+  double best = 1e30;
+  for (int chunks = 1; chunks <= nz; ++chunks) {
+    const int z = (nz + chunks - 1) / chunks;
+    if (z < min_zchunk(nz)) break;
+    if (z > 64) continue;  // long chunks leave too few CTAs to overlap their pipelines
+    const long long nchunks = (nz + z - 1) / z;
+    const double waves = double(tiles * nchunks) / resident;
+    const double busy = waves / std::ceil(waves);
+    const double cost = (1.0 + 2.0 / z) / busy;
+    if (cost < best - 1e-9) {
+      best = cost;
+      zc = z;
+    }
+  }
+  return std::min(zc, nz);
+}
+
+// Row split for walls that occupy few rows (a channel's walls): row y is clean when rows y-1, y,
+// y+1 (periodic) hold no solid site at any x and z, so every population its outputs pull comes
+// from a fluid site and the periodic kernel (no mask logic) computes them exactly. When the clean
+// rows form one cyclic run of at least half the rows, that run goes to the line-aligned periodic
+// kernel and the remaining rows to the masked kernel. Only where the aligned kernel is the one
+// the library picks for periodic lattices of this size and type.
+lbf_status setup_split(lbf_ctx* c, const lbf_params* p, const Layout& L, int sms, bool nearest,
+                       const std::string& kname) {
+  if (!c->has_mask || c->two || c->pops || !c->tma || c->aligned || p->force_field != nullptr || LBF_AL_TMA_STORE ||
+      kname == "cta" || kname == "aligned")
+    return LBF_OK;
+  const long long plane_sites = (long long)c->nx * c->ny;
+  const bool q19_f32 = c->Q == LBF_D3Q19 && c->storage == LBF_F32;
+  const bool forced = kname == "split";  // LBF_KERNEL=split: any plane size (tests)
+  if ((!forced && plane_sites < (q19_f32 ? 256LL * 256LL : 512LL * 512LL)) ||
+      !((c->Q == LBF_D3Q19 && c->storage != LBF_F64) || (c->Q == LBF_D3Q27 && c->storage == LBF_F32)))
+    return LBF_OK;
+  const KernelInfo al = aligned_kernel_for(c->Q, c->storage, false, false, nearest);
+  if (al.fn == nullptr) return LBF_OK;
+  const int nx = c->nx, ny = c->ny, nz = c->nz;
+  std::vector<char> solid_row(ny, 0);
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y) {
+      if (solid_row[y]) continue;
+      const uint8_t* row = p->mask + ((long long)z * ny + y) * nx;
+      for (int x = 0; x < nx; ++x)
+        if (row[x] != 0) {
+          solid_row[y] = 1;
+          break;
+        }
+    }
+  std::vector<char> clean(ny);
+  int nclean = 0;
+  for (int y = 0; y < ny; ++y) {
+    clean[y] = !(solid_row[(y + ny - 1) % ny] || solid_row[y] || solid_row[(y + 1) % ny]);
+    nclean += clean[y];
+  }
+  if (nclean == ny || nclean < ny / 2) return LBF_OK;  // no solid site at all, or walls everywhere
+  // the longest cyclic run of clean rows starts right after a row that is not clean
+  int best_begin = 0, best_len = 0;
+  for (int y = 0; y < ny; ++y) {
+    if (!clean[y] || clean[(y + ny - 1) % ny]) continue;
+    int len = 0;
+    while (len < ny && clean[(y + len) % ny]) ++len;
+    if (len > best_len) best_len = len, best_begin = y;
+  }
+  if (best_len < ny / 2 || best_len < 2 * al.by) return LBF_OK;
+  lbf_status st;
+  if ((st = prepare(al)) != LBF_OK) return st;
+  int per_sm_al = 1, per_sm_m = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_al, al.fn, al.threads, al.smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_m, c->fwd.fn, c->fwd.threads, c->fwd.smem) != cudaSuccess)
+    return fail(LBF_ECUDA, std::string("device query failed: ") + cudaGetErrorString(cudaGetLastError()));
+  const int dirty_rows = ny - best_len;
+  const long long tiles_clean = (long long)grid_x(nx, al.xout) * grid_y(best_len, al.by);
+  const long long tiles_dirty = (long long)grid_x(nx, c->fwd.xout) * grid_y(dirty_rows, c->fwd.by);
+  const int zcc = choose_zchunk(nz, tiles_clean, double(sms) * std::max(per_sm_al, 1));
+  // the rows near walls run beside the clean launch: short chunks, so that they finish early
+  const int zcd = std::min(min_zchunk(nz), nz);
+  const dim3 gc(grid_x(nx, al.xout), grid_y(best_len, al.by), (nz + zcc - 1) / zcc);
+  const dim3 gd(grid_x(nx, c->fwd.xout), grid_y(dirty_rows, c->fwd.by), (nz + zcd - 1) / zcd);
+  const long long blocks = (long long)gc.x * gc.y * gc.z + (long long)gd.x * gd.y * gd.z;
+  if (blocks > L.npartials) return LBF_OK;
+  for (int k = 0; k < 2; ++k)
+    if ((st = encode_state_map(c, c->state[k], &c->tmap_clean[k], al.box_x, al.by + 2)) != LBF_OK) return st;
+  int lo = 0, hi = 0;
+  LBF_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  LBF_CUDA(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi));  // dispatched first
+  LBF_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  LBF_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  c->fwd_clean = al;
+  c->clean_begin = best_begin;
+  c->clean_rows = best_len;
+  c->dirty_begin = (best_begin + best_len) % ny;
+  c->dirty_rows = dirty_rows;
+  c->zchunk_clean = zcc;
+  c->zchunk_dirty = zcd;
+  c->grid_clean = gc;
+  c->grid_dirty = gd;
+  c->split = true;
+  return LBF_OK;
+}
+
+// one step as two launches over row ranges: the rows near walls (masked kernel) on the side stream,
+// the clean rows (periodic line-aligned kernel) on the context's stream, joined before the sums
+lbf_status launch_split(lbf_ctx* c, const FwdParams& a, int ks, bool reduce) {
+  FwdParams ad = a, ac = a;
+  ad.y_begin = c->dirty_begin;
+  ad.y_rows = c->dirty_rows;
+  ad.zchunk = c->zchunk_dirty;
+  ad.block_base = 0;
+  ad.no_final = 1;
+  ac.y_begin = c->clean_begin;
+  ac.y_rows = c->clean_rows;
+  ac.zchunk = c->zchunk_clean;
+  ac.block_base = (long long)c->grid_dirty.x * c->grid_dirty.y * c->grid_dirty.z;
+  ac.no_final = 1;
+  ac.mask = nullptr;  // every site of the clean rows and of their neighbour rows is fluid
+  CUtensorMap tmd = c->tmap[ks], tmc = c->tmap_clean[ks], none;
+  std::memset(&none, 0, sizeof(none));
+  LBF_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+  LBF_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  void* argd[] = {&ad, &tmd, &none};
+  LBF_CUDA(cudaLaunchKernel(c->fwd.fn, c->grid_dirty, dim3(32, c->fwd.threads / 32, 1), argd, c->fwd.smem, c->side));
+  LBF_CUDA(cudaEventRecord(c->ev_join, c->side));
+  void* argc[] = {&ac, &tmc, &none};
+  LBF_CUDA(cudaLaunchKernel(c->fwd_clean.fn, c->grid_clean, dim3(32, c->fwd_clean.threads / 32, 1), argc,
+                            c->fwd_clean.smem, c->stream));
+  LBF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  if (reduce) {
+    const long long nall = ac.block_base + (long long)c->grid_clean.x * c->grid_clean.y * c->grid_clean.z;
+    k_reduce_final<<<1, 256, 0, c->stream>>>(c->partials, nall, c->sums);
+    LBF_CUDA(cudaGetLastError());
+  }
+  return LBF_OK;
+}
+
 lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
   if (c->pops) {
     PopParams pp = pop_params(c, src, dst, reduce);
@@ -488,6 +638,11 @@ lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
   }
   FwdParams a = forward_params(c, src, dst, reduce);
   ++c->steps_done;
+  if (c->split) {
+    const int ks = src == c->state[0] ? 0 : (src == c->state[1] ? 1 : -1);
+    const int kd = dst == c->state[0] ? 0 : (dst == c->state[1] ? 1 : -1);
+    if (ks >= 0 && kd >= 0) return launch_split(c, a, ks, reduce);
+  }
   CUtensorMap tm, sm;
   std::memset(&tm, 0, sizeof(tm));
   std::memset(&sm, 0, sizeof(sm));
@@ -528,8 +683,6 @@ lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
   LBF_CUDA(cudaLaunchKernel(k->fn, grid, dim3(32, k->threads / 32, 1), args, k->smem, c->stream));
   return LBF_OK;
 }
-
-long long forward_blocks(const lbf_ctx* c) { return (long long)c->fgrid.x * c->fgrid.y * c->fgrid.z; }
 
 lbf_status finalize_sums(lbf_ctx* c, long long nblocks) {
   k_reduce_final<<<1, 256, 0, c->stream>>>(c->partials, nblocks, c->sums);
@@ -611,6 +764,11 @@ void lbf_internal_set_last_error(const char* msg) { g_last_error = msg ? msg : "
 extern "C" {
 
 int lbf_version(void) { return 1; }
+
+int lbf_kernels_per_step(const lbf_ctx* c) {
+  if (c == nullptr) return 0;
+  return (c->split ? 3 : 1) + (c->two ? 2 : 0);
+}
 
 const char* lbf_last_error(void) { return g_last_error.c_str(); }
 
@@ -730,7 +888,7 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
     return fail(LBF_ENOTSUP, "no kernel for this combination");
   }
   auto cleanup = [&](lbf_status s) {
-    delete c;
+    lbf_destroy(c);
     return s;
   };
   if ((st = prepare(c->fwd)) != LBF_OK) return cleanup(st);
@@ -747,22 +905,7 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
     return cleanup(fail(LBF_ECUDA, std::string("device query failed: ") + cudaGetErrorString(cudaGetLastError())));
   per_sm = std::max(per_sm, 1);
   const long long tiles = (long long)grid_x(c->nx, c->fwd.xout) * grid_y(c->ny, c->fwd.by);
-  const double resident = double(sms) * per_sm;
-  int zc = c->nz;
-  double best = 1e30;
-  for (int chunks = 1; chunks <= c->nz; ++chunks) {
-    const int z = (c->nz + chunks - 1) / chunks;
-    if (z < min_zchunk(c->nz)) break;
-    if (z > 64) continue;  // long chunks leave too few CTAs to overlap their pipelines
-    const long long nchunks = (c->nz + z - 1) / z;
-    const double waves = double(tiles * nchunks) / resident;
-    const double busy = waves / std::ceil(waves);
-    const double cost = (1.0 + 2.0 / z) / busy;
-    if (cost < best - 1e-9) {
-      best = cost;
-      zc = z;
-    }
-  }
+  int zc = choose_zchunk(c->nz, tiles, double(sms) * per_sm);
   if (const char* e = std::getenv("LBF_ZCHUNK")) {
     const int v = std::atoi(e);
     if (v >= 1) zc = std::max(min_zchunk(c->nz), v);
@@ -781,6 +924,7 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
   for (const KernelInfo* k : {&c->fwd, &c->fwd_tma30, &c->fwd_direct})
     if ((long long)grid_x(c->nx, k->xout) * grid_y(c->ny, k->by) * gz > L.npartials)
       return cleanup(fail(LBF_EINTERNAL, "partials buffer too small"));
+  if ((st = setup_split(c, params, L, sms, nearest, kname)) != LBF_OK) return cleanup(st);
 
   cudaStream_t s = c->stream;
   if (cudaMemsetAsync(c->state[0], 0, 10 * c->N * storage_bytes(c->storage), s) != cudaSuccess ||
@@ -809,6 +953,12 @@ lbf_status lbf_create(lbf_ctx** out, const lbf_params* params, void* workspace, 
 }
 
 lbf_status lbf_destroy(lbf_ctx* c) {
+  if (c != nullptr && c->side != nullptr) {
+    cudaStreamSynchronize(c->side);
+    cudaEventDestroy(c->ev_fork);
+    cudaEventDestroy(c->ev_join);
+    cudaStreamDestroy(c->side);
+  }
   delete c;
   return LBF_OK;
 }

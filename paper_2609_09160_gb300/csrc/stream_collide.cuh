@@ -64,6 +64,12 @@ struct FwdParams {
   int zchunk;
   float umax2;
   uint32_t salt;            // per-step word mixed into the stochastic rounding of 16-bit storage
+  // output rows of this launch: y_begin .. y_begin + y_rows - 1, taken mod ny (y_rows = 0: all ny
+  // rows from 0). The blocks' partial sums go to partials[block_base + block]; no_final = 1 leaves
+  // the final sum to a later kernel (launches over row ranges that run concurrently)
+  int y_begin, y_rows;
+  long long block_base;
+  int no_final;
   // FP32 copies of the double scalars above (set_fp32_copies), read by the FP32-compute kernels
   float force_f[3], omega_f, rho_l_f, drho_f, nu_l_f, dnu_f;
 };
@@ -575,14 +581,17 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
 
   const int lane = threadIdx.x, row = threadIdx.y;
   const int x0 = blockIdx.x * FwdTile<BY>::XOUT;
+  const int yb = a.y_begin, yrows = a.y_rows > 0 ? a.y_rows : a.ny;
+  const int ty0 = yb + int(blockIdx.y) * BY;  // first output row of the tile (may exceed ny: wraps)
   const int gx = x0 - 1 + lane;
-  const int gy = blockIdx.y * BY - 1 + row;
+  const int gy = ty0 - 1 + row;
+  const int ly = gy - yb;                     // row within this launch's range
   const int sx = ((gx % a.nx) + a.nx) % a.nx;
   const int sy = ((gy % a.ny) + a.ny) % a.ny;
   const bool out_row = row >= 1 && row <= BY;  // warp-uniform
-  const bool outcol = out_row && lane >= 1 && lane <= FwdTile<BY>::XOUT && gx < a.nx && gy < a.ny;
+  const bool outcol = out_row && lane >= 1 && lane <= FwdTile<BY>::XOUT && gx < a.nx && ly < yrows;
   const bool inbox = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;  // TMA delivers this site
-  const bool needed = gx <= a.nx && gy <= a.ny;                      // read by some output
+  const bool needed = gx <= a.nx && ly <= yrows;                     // read by some output
   const int xa = ((x0 - 1 + AL) / AL - 1) * AL;                      // floor to AL; x0 - 1 >= -1
   const int xoff = x0 - 1 - xa;
   const long long plane = (long long)a.nx * a.ny;
@@ -613,7 +622,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     // completed before the barrier that precedes this call
     LBF_CHECK(a.flags, (xa * int(sizeof(S))) % 16 == 0 && s >= 0 && s < kRawStages);
     mbar_arrive_expect_tx(&bars[s], uint32_t(STAGE_ELEMS * sizeof(S)));
-    tma_load_4d(dstp, &tmap, &bars[s], xa, int(blockIdx.y) * BY - 1, wrap(p, a.nz), 0);
+    tma_load_4d(dstp, &tmap, &bars[s], xa, ty0 - 1, wrap(p, a.nz), 0);
     issued = p;
   };
   auto wait_plane = [&](int p) {
@@ -1095,7 +1104,7 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     if (me < 6) {
       double s = 0.0;
       for (int r = 0; r < ROWS; ++r) s += red_s[r * 6 + me];
-      const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      const long long b = a.block_base + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
       a.partials[b * 8 + me] = s;
     }
     // second stage in the same launch: the last block to finish sums the partials in a fixed
@@ -1104,17 +1113,18 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     __shared__ bool last;
     __threadfence();
     __syncthreads();
-    if (me == 0) last = atomicAdd(a.counter, 1u) == (unsigned)(nb - 1);
+    if (me == 0) last = !a.no_final && atomicAdd(a.counter, 1u) == (unsigned)(nb - 1);
     __syncthreads();
     if (last) {
       __threadfence();
       constexpr int NT = FwdTile<BY>::THREADS;
+      const long long nall = a.block_base + nb;  // partials of the launches before this one, then its own
       double* tree = reinterpret_cast<double*>(smem_raw);
       for (int i = me; i < 6 * 512; i += NT) tree[i] = 0.0;
       __syncthreads();
       for (int k = 0; k < 6; ++k) {
         double acc = 0.0;
-        for (long long b = me; b < nb; b += NT) acc += __ldcg(a.partials + b * 8 + k);
+        for (long long b = me; b < nall; b += NT) acc += __ldcg(a.partials + b * 8 + k);
         tree[k * 512 + me] = acc;
       }
       __syncthreads();

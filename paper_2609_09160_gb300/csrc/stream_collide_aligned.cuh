@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
   const T* __restrict__ ffield = static_cast<const T*>(a.force_field);
 
   const int lane = threadIdx.x, warp = threadIdx.y;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
+  const int yb = a.y_begin, yrows = a.y_rows > 0 ? a.y_rows : a.ny;  // this launch's output rows
+  const int x0 = blockIdx.x * 32, y0 = yb + int(blockIdx.y) * TY;     // y0 may exceed ny: wraps
   // this thread's staged site: ring row rr, ring column rc; role 0 = output row (every direction),
   // 1 / 2 = y halo below / above (c_y = +1 / -1), 3 / 4 = x halo left / right (c_x = +1 / -1),
   // 5 = nothing to stage
@@ -190,9 +191,9 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
   const int sx = ((gx % a.nx) + a.nx) % a.nx;
   const int sy = ((gy % a.ny) + a.ny) % a.ny;
   const bool out_row = warp < TY;  // warp-uniform
-  const bool outcol = out_row && x0 + lane < a.nx && y0 + warp < a.ny;
+  const bool outcol = out_row && x0 + lane < a.nx && (y0 - yb) + warp < yrows;
   const bool inbox = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;  // TMA delivers this site
-  const bool needed = role != 5 && gx <= a.nx && gy <= a.ny;          // read by some output
+  const bool needed = role != 5 && gx <= a.nx && gy - yb <= yrows;    // read by some output
   const long long plane = (long long)a.nx * a.ny;
   const int col = sy * a.nx + sx;
   const long long N = a.N;
@@ -621,23 +622,24 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
     if (tid < 6) {
       double s = 0.0;
       for (int r = 0; r < G::WARPS; ++r) s += red_s[r * 6 + tid];
-      const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      const long long b = a.block_base + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
       a.partials[b * 8 + tid] = s;
     }
     __shared__ bool last;
     __threadfence();
     __syncthreads();
-    if (tid == 0) last = atomicAdd(a.counter, 1u) == (unsigned)(nb - 1);
+    if (tid == 0) last = !a.no_final && atomicAdd(a.counter, 1u) == (unsigned)(nb - 1);
     __syncthreads();
     if (last) {
       __threadfence();
       constexpr int NT = G::THREADS;
+      const long long nall = a.block_base + nb;
       double* tree = reinterpret_cast<double*>(sbase);
       for (int i = tid; i < 6 * 512; i += NT) tree[i] = 0.0;
       __syncthreads();
       for (int k = 0; k < 6; ++k) {
         double acc = 0.0;
-        for (long long b = tid; b < nb; b += NT) acc += __ldcg(a.partials + b * 8 + k);
+        for (long long b = tid; b < nall; b += NT) acc += __ldcg(a.partials + b * 8 + k);
         tree[k * 512 + tid] = acc;
       }
       __syncthreads();

@@ -147,6 +147,11 @@ class Solver:
         _lbf.lbf_reduce_async(self.ctx, out.data_ptr())
         return out
 
+    @property
+    def kernels_per_step(self):
+        """Kernel launches one step issues (1; 3 with the row split for walls; +2 two components)."""
+        return _lbf.lbf_kernels_per_step(self.ctx)
+
     def synchronize(self):
         _lbf.lbf_synchronize(self.ctx)
 
