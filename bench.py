@@ -553,9 +553,9 @@ def kernel_label(s, lattice, storage, kind):
     """The kernels one timed step runs (the roofline unit is one step: its launches together)."""
     lat = LATTICE_NAME[lattice]
     walls = kind in ("channel", "layered")
-    if s.kernels_per_step == 3 and walls and kind == "channel":
+    if s.kernels_per_step == 2 and kind == "channel":
         return (f"k_stream_collide_al<{lat},{storage},periodic> on the rows clear of the walls + "
-                f"k_stream_collide<{lat},{storage},mask> on the rows near them + k_reduce_final")
+                f"k_stream_collide<{lat},{storage},mask> on the rows near them")
     fused = f"k_stream_collide<{lat},{storage},{'mask' if walls else 'periodic'}>"
     if kind in ("droplet", "layered"):
         return f"k_phase_advance + k_phase_forces + {fused}"

@@ -179,10 +179,10 @@ lbf_status lbf_reduce_async(lbf_ctx* ctx, double* dst);
    Paper: no counterpart (stream completion and the library's instability check). */
 lbf_status lbf_synchronize(lbf_ctx* ctx);
 
-/* Kernel launches one time step of lbf_step issues with this context's configuration, including
-   the FP64 sums the step computes: 1 for the fused step, 3 when walls in a band of rows split it
-   (rows near walls, clean rows, final sums), plus 2 with two components (phase-field advance and
-   forces). 0 for a NULL context.
+/* Kernel launches one time step of lbf_step issues with this context's configuration, the FP64
+   sums included: 1 for the fused step, 2 when walls in a band of rows split it (the rows near the
+   walls on a side stream, the other rows on the context's stream), plus 2 with two components
+   (phase-field advance and forces). 0 for a NULL context.
    Paper: no counterpart (launch structure of the implementation). */
 int lbf_kernels_per_step(const lbf_ctx* ctx);
 

@@ -220,7 +220,7 @@ struct lbf_ctx {
   dim3 pop_grid;                  // pops: (ceil(nx / 256), ny, nz) blocks of 256 threads
   // walls confined to a band of rows: the rows clear of every solid site and of its neighbours
   // ("clean") run the periodic line-aligned kernel, the others the masked 30-column kernel on a
-  // side stream; a one-block kernel then adds both launches' partial sums
+  // side stream; the last block of either launch adds both launches' partial sums
   bool split;
   int clean_begin, clean_rows, dirty_begin, dirty_rows;
   KernelInfo fwd_clean;
@@ -512,6 +512,10 @@ int choose_zchunk(int nz, long long tiles, double resident) {
   return std::min(zc, nz);
 }
 
+#ifndef LBF_SPLIT_ZCHUNK
+#define LBF_SPLIT_ZCHUNK 32
+#endif
+
 // Row split for walls that occupy few rows (a channel's walls): row y is clean when rows y-1, y,
 // y+1 (periodic) hold no solid site at any x and z, so every population its outputs pull comes
 // from a fluid site and the periodic kernel (no mask logic) computes them exactly. When the clean
@@ -569,8 +573,8 @@ lbf_status setup_split(lbf_ctx* c, const lbf_params* p, const Layout& L, int sms
   const long long tiles_clean = (long long)grid_x(nx, al.xout) * grid_y(best_len, al.by);
   const long long tiles_dirty = (long long)grid_x(nx, c->fwd.xout) * grid_y(dirty_rows, c->fwd.by);
   const int zcc = choose_zchunk(nz, tiles_clean, double(sms) * std::max(per_sm_al, 1));
-  // the rows near walls run beside the clean launch: short chunks, so that they finish early
-  const int zcd = std::min(min_zchunk(nz), nz);
+  // the rows near walls run beside the clean launch on a few CTAs (tuning define LBF_SPLIT_ZCHUNK)
+  const int zcd = std::min(LBF_SPLIT_ZCHUNK, nz);
   const dim3 gc(grid_x(nx, al.xout), grid_y(best_len, al.by), (nz + zcc - 1) / zcc);
   const dim3 gd(grid_x(nx, c->fwd.xout), grid_y(dirty_rows, c->fwd.by), (nz + zcd - 1) / zcd);
   const long long blocks = (long long)gc.x * gc.y * gc.z + (long long)gd.x * gd.y * gd.z;
@@ -596,19 +600,22 @@ lbf_status setup_split(lbf_ctx* c, const lbf_params* p, const Layout& L, int sms
 }
 
 // one step as two launches over row ranges: the rows near walls (masked kernel) on the side stream,
-// the clean rows (periodic line-aligned kernel) on the context's stream, joined before the sums
-lbf_status launch_split(lbf_ctx* c, const FwdParams& a, int ks, bool reduce) {
+// the clean rows (periodic line-aligned kernel) on the context's stream, joined at the end of the
+// step; the two launches share the block counter, and the last block of either adds all partials
+lbf_status launch_split(lbf_ctx* c, const FwdParams& a, int ks) {
   FwdParams ad = a, ac = a;
+  const long long nd = (long long)c->grid_dirty.x * c->grid_dirty.y * c->grid_dirty.z;
+  const long long nc = (long long)c->grid_clean.x * c->grid_clean.y * c->grid_clean.z;
   ad.y_begin = c->dirty_begin;
   ad.y_rows = c->dirty_rows;
   ad.zchunk = c->zchunk_dirty;
   ad.block_base = 0;
-  ad.no_final = 1;
+  ad.final_blocks = nd + nc;
   ac.y_begin = c->clean_begin;
   ac.y_rows = c->clean_rows;
   ac.zchunk = c->zchunk_clean;
-  ac.block_base = (long long)c->grid_dirty.x * c->grid_dirty.y * c->grid_dirty.z;
-  ac.no_final = 1;
+  ac.block_base = nd;
+  ac.final_blocks = nd + nc;
   ac.mask = nullptr;  // every site of the clean rows and of their neighbour rows is fluid
   CUtensorMap tmd = c->tmap[ks], tmc = c->tmap_clean[ks], none;
   std::memset(&none, 0, sizeof(none));
@@ -621,11 +628,6 @@ lbf_status launch_split(lbf_ctx* c, const FwdParams& a, int ks, bool reduce) {
   LBF_CUDA(cudaLaunchKernel(c->fwd_clean.fn, c->grid_clean, dim3(32, c->fwd_clean.threads / 32, 1), argc,
                             c->fwd_clean.smem, c->stream));
   LBF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-  if (reduce) {
-    const long long nall = ac.block_base + (long long)c->grid_clean.x * c->grid_clean.y * c->grid_clean.z;
-    k_reduce_final<<<1, 256, 0, c->stream>>>(c->partials, nall, c->sums);
-    LBF_CUDA(cudaGetLastError());
-  }
   return LBF_OK;
 }
 
@@ -641,7 +643,7 @@ lbf_status launch_forward(lbf_ctx* c, const void* src, void* dst, bool reduce) {
   if (c->split) {
     const int ks = src == c->state[0] ? 0 : (src == c->state[1] ? 1 : -1);
     const int kd = dst == c->state[0] ? 0 : (dst == c->state[1] ? 1 : -1);
-    if (ks >= 0 && kd >= 0) return launch_split(c, a, ks, reduce);
+    if (ks >= 0 && kd >= 0) return launch_split(c, a, ks);
   }
   CUtensorMap tm, sm;
   std::memset(&tm, 0, sizeof(tm));
@@ -767,7 +769,7 @@ int lbf_version(void) { return 1; }
 
 int lbf_kernels_per_step(const lbf_ctx* c) {
   if (c == nullptr) return 0;
-  return (c->split ? 3 : 1) + (c->two ? 2 : 0);
+  return (c->split ? 2 : 1) + (c->two ? 2 : 0);
 }
 
 const char* lbf_last_error(void) { return g_last_error.c_str(); }

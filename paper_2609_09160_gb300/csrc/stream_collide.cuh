@@ -65,11 +65,12 @@ struct FwdParams {
   float umax2;
   uint32_t salt;            // per-step word mixed into the stochastic rounding of 16-bit storage
   // output rows of this launch: y_begin .. y_begin + y_rows - 1, taken mod ny (y_rows = 0: all ny
-  // rows from 0). The blocks' partial sums go to partials[block_base + block]; no_final = 1 leaves
-  // the final sum to a later kernel (launches over row ranges that run concurrently)
+  // rows from 0). The blocks' partial sums go to partials[block_base + block]; final_blocks > 0:
+  // launches that run concurrently share the block counter, and the last of their final_blocks
+  // blocks to finish adds partials 0 .. final_blocks - 1 (0: this launch alone, block_base + blocks)
   int y_begin, y_rows;
   long long block_base;
-  int no_final;
+  long long final_blocks;
   // FP32 copies of the double scalars above (set_fp32_copies), read by the FP32-compute kernels
   float force_f[3], omega_f, rho_l_f, drho_f, nu_l_f, dnu_f;
 };
@@ -1113,12 +1114,12 @@ __global__ void __launch_bounds__(FwdTile<BY>::THREADS, fwd_minb(L::Q, int(sizeo
     __shared__ bool last;
     __threadfence();
     __syncthreads();
-    if (me == 0) last = !a.no_final && atomicAdd(a.counter, 1u) == (unsigned)(nb - 1);
+    const long long nall = a.final_blocks > 0 ? a.final_blocks : a.block_base + nb;  // partials to add
+    if (me == 0) last = atomicAdd(a.counter, 1u) == (unsigned)(a.final_blocks > 0 ? nall - 1 : nb - 1);
     __syncthreads();
     if (last) {
       __threadfence();
       constexpr int NT = FwdTile<BY>::THREADS;
-      const long long nall = a.block_base + nb;  // partials of the launches before this one, then its own
       double* tree = reinterpret_cast<double*>(smem_raw);
       for (int i = me; i < 6 * 512; i += NT) tree[i] = 0.0;
       __syncthreads();

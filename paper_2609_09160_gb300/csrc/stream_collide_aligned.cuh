@@ -628,12 +628,12 @@ __global__ void __launch_bounds__(AlTile<S, TY>::THREADS, al_minb<L, S, TY, MASK
     __shared__ bool last;
     __threadfence();
     __syncthreads();
-    if (tid == 0) last = !a.no_final && atomicAdd(a.counter, 1u) == (unsigned)(nb - 1);
+    const long long nall = a.final_blocks > 0 ? a.final_blocks : a.block_base + nb;  // partials to add
+    if (tid == 0) last = atomicAdd(a.counter, 1u) == (unsigned)(a.final_blocks > 0 ? nall - 1 : nb - 1);
     __syncthreads();
     if (last) {
       __threadfence();
       constexpr int NT = G::THREADS;
-      const long long nall = a.block_base + nb;
       double* tree = reinterpret_cast<double*>(sbase);
       for (int i = tid; i < 6 * 512; i += NT) tree[i] = 0.0;
       __syncthreads();

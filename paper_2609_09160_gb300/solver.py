@@ -149,7 +149,7 @@ class Solver:
 
     @property
     def kernels_per_step(self):
-        """Kernel launches one step issues (1; 3 with the row split for walls; +2 two components)."""
+        """Kernel launches one step issues (1; 2 with the row split for walls; +2 two components)."""
         return _lbf.lbf_kernels_per_step(self.ctx)
 
     def synchronize(self):
