@@ -572,7 +572,11 @@ lbf_status setup_split(lbf_ctx* c, const lbf_params* p, const Layout& L, int sms
   const int dirty_rows = ny - best_len;
   const long long tiles_clean = (long long)grid_x(nx, al.xout) * grid_y(best_len, al.by);
   const long long tiles_dirty = (long long)grid_x(nx, c->fwd.xout) * grid_y(dirty_rows, c->fwd.by);
-  const int zcc = choose_zchunk(nz, tiles_clean, double(sms) * std::max(per_sm_al, 1));
+  int zcc = choose_zchunk(nz, tiles_clean, double(sms) * std::max(per_sm_al, 1));
+  if (const char* e = std::getenv("LBF_ZCHUNK")) {  // the same override as for a single launch
+    const int v = std::atoi(e);
+    if (v >= 1) zcc = std::min(nz, std::max(min_zchunk(nz), v));
+  }
   // the rows near walls run beside the clean launch on a few CTAs (tuning define LBF_SPLIT_ZCHUNK)
   const int zcd = std::min(LBF_SPLIT_ZCHUNK, nz);
   const dim3 gc(grid_x(nx, al.xout), grid_y(best_len, al.by), (nz + zcc - 1) / zcc);
