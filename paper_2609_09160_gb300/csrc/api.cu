@@ -574,6 +574,13 @@ lbf_status setup_split(lbf_ctx* c, const lbf_params* p, const Layout& L, int sms
     while (len < ny && clean[(y + len) % ny]) ++len;
     if (len > best_len) best_len = len, best_begin = y;
   }
+  // whole tiles on both sides where possible: the clean run shrinks to a multiple of the aligned
+  // tile height such that the rows left to the masked kernel fill whole tiles of its own height
+  for (int len = best_len / al.by * al.by; len >= 2 * al.by && len >= ny / 2; len -= al.by)
+    if ((ny - len) % c->fwd.by == 0) {
+      best_len = len;
+      break;
+    }
   if (best_len < ny / 2 || best_len < 2 * al.by) return LBF_OK;
   lbf_status st;
   if ((st = prepare(al)) != LBF_OK) return st;
