@@ -556,7 +556,8 @@ def kernel_label(s, lattice, storage, kind):
     if s.kernels_per_step == 2 and kind == "channel":
         return (f"k_stream_collide_al<{lat},{storage},periodic> on the rows clear of the walls + "
                 f"k_stream_collide<{lat},{storage},mask> on the rows near them")
-    fused = f"k_stream_collide<{lat},{storage},{'mask' if walls else 'periodic'}>"
+    fused = (f"k_stream_collide<{lat},{storage},{'mask' if walls else 'periodic'}>" if walls or kind == "droplet"
+             else f"k_stream_collide_al or k_stream_collide<{lat},{storage},periodic> (the library's choice)")
     if kind in ("droplet", "layered"):
         return f"k_phase_advance + k_phase_forces + {fused}"
     return fused
