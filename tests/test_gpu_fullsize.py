@@ -1,5 +1,5 @@
-"""Full-size checks in the benchmark's launch configuration: the 256^3 D3Q19 channel (FP32) and
-the 512^3 D3Q27 Taylor-Green (FP32 and FP16 storage). The oracle recomputes one step at sampled
+"""Full-size checks in the benchmark's launch configuration: the 256^3 D3Q19 channel (FP32; the row
+split of the library, also on a 512^3 channel) and the 512^3 D3Q27 Taylor-Green (FP32 and FP16 storage). The oracle recomputes one step at sampled
 sites - at random, next to the walls and on CTA tile seams - from the GPU's own state before
 that step; properties that hold at any size (mass conservation) are checked on the whole box."""
 import numpy as np
@@ -66,12 +66,28 @@ def test_channel_256_d3q19_fp32_sampled():
     s.set_moments(M0.to(torch.float32).cuda())
     r0 = s.reduce()
     s.step(20)
+    # 30-column tile seams (masked kernel), the row split's boundaries (rows 249 | 250 and 1 | 2: the
+    # periodic line-aligned kernel runs rows 2..249), its 32 x 8 tile seams and z-chunk seams
     seams = [(7, 1, 0), (7, 1, 29), (7, 1, 30), (8, 254, 255), (100, 8, 59), (100, 9, 60), (255, 255, 17),
-             (0, 128, 240), (63, 64, 241), (64, 65, 239)]
+             (0, 128, 240), (63, 64, 241), (64, 65, 239), (21, 249, 31), (22, 250, 32), (43, 1, 63), (44, 2, 64),
+             (0, 9, 95), (100, 10, 96), (255, 253, 128), (128, 254, 31), (21, 2, 255), (22, 249, 0)]
     check_one_step(s, LAT[19], 0.9, (1e-6, 0.0, 0.0), sample_sites(shape, 3000, 2, seams), solid)
     r1 = s.reduce()
     assert abs(r1[0] - r0[0]) < 1e-6 * M0[0].abs().sum().item()
     assert r1[1] > 0  # the body force accelerates the fluid along +x
+
+
+def test_channel_512_d3q19_fp32_sampled():
+    """The row split on a 512^3 channel: rows 2..505 on the periodic line-aligned kernel, rows
+    506..511, 0, 1 on the masked kernel beside it."""
+    shape = (512, 512, 512)
+    M0, solid = synth.channel(shape, 1e-3, seed=5)
+    s = Solver(shape, lattice=19, tau=0.9, storage="f32", force=(1e-6, 0.0, 0.0), mask=solid)
+    s.set_moments(M0.to(torch.float32).cuda())
+    del M0
+    s.step(3)
+    seams = [(63, 505, 31), (64, 506, 32), (0, 1, 511), (511, 2, 0), (300, 9, 63), (301, 10, 64), (5, 510, 200)]
+    check_one_step(s, LAT[19], 0.9, (1e-6, 0.0, 0.0), sample_sites(shape, 2000, 6, seams), solid)
 
 
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16", 2e-3)])
