@@ -584,9 +584,8 @@ lbf_status setup_split(lbf_ctx* c, const lbf_params* p, const Layout& L, int sms
   if (best_len < ny / 2 || best_len < 2 * al.by) return LBF_OK;
   lbf_status st;
   if ((st = prepare(al)) != LBF_OK) return st;
-  int per_sm_al = 1, per_sm_m = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_al, al.fn, al.threads, al.smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_m, c->fwd.fn, c->fwd.threads, c->fwd.smem) != cudaSuccess)
+  int per_sm_al = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_al, al.fn, al.threads, al.smem) != cudaSuccess)
     return fail(LBF_ECUDA, std::string("device query failed: ") + cudaGetErrorString(cudaGetLastError()));
   const int dirty_rows = ny - best_len;
   const long long tiles_clean = (long long)grid_x(nx, al.xout) * grid_y(best_len, al.by);

@@ -10,6 +10,7 @@ import synth
 from paper_2609_09160_gb300 import LBFError, Solver
 
 SHAPES = [(1, 1, 1), (3, 5, 7), (5, 9, 31), (4, 17, 36), (6, 10, 64), (9, 26, 40), (3, 8, 33)]
+SPLIT_SHAPES = [(3, 30, 64), (2, 41, 40), (5, 26, 96), (9, 26, 40)]
 
 
 def cases():
@@ -20,6 +21,11 @@ def cases():
                     continue
                 for shape in SHAPES:
                     yield lattice, storage, kind, shape, "cta"
+    # the row split (walls at y = 0 and ny - 1: clean rows on the line-aligned kernel, the rows at
+    # the walls on the masked 30-column kernel), on shapes whose clean run is long enough for it
+    for lattice, storage in ((19, "f32"), (19, "f16"), (27, "f32")):
+        for shape in SPLIT_SHAPES:
+            yield lattice, storage, "split", shape, "split"
     # the line-aligned kernel (single component, FP32 and 16-bit storage) on the same shapes
     for lattice in (19, 27):
         for storage in ("f32", "f16", "bf16"):
@@ -34,6 +40,9 @@ def run(lattice, storage, kind, shape, kernel):
     kw = {}
     if kind == "walls":
         kw["mask"] = synth.random_mask(shape, 0.2, seed=5)
+        kw["force"] = (1e-5, 0.0, 0.0)
+    elif kind == "split":
+        kw["mask"] = synth.channel_walls(shape)
         kw["force"] = (1e-5, 0.0, 0.0)
     elif kind == "field":
         kw["force_field"] = (1e-5 * torch.randn((3,) + shape, generator=torch.Generator().manual_seed(6))).to(
